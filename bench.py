@@ -1,0 +1,377 @@
+"""Benchmark: unfused gate application on a 28-qubit complex64 state.
+
+Workload (the paper's headline measurement is utilised HBM bandwidth of gate
+application, Sec. II-B): a 28-qubit random circuit of depth 40 -- per layer a
+Haar SU(2) on every qubit, then CZ / CNOT / CRZ on 14 random disjoint pairs --
+applied one gate per launch to a 2 GiB complex64 state resident in HBM, then
+<Z_q> for every qubit, 8 random Pauli strings and one parity measurement.
+One step = that whole pass (1680 gate launches + the reductions).
+
+value = algorithmic bytes moved per step / step time (GB/s): a dense one-qubit
+gate reads and writes every amplitude (16 B per amplitude); CNOT and CRZ touch
+the half where the control is 1; CZ the quarter where both bits are 1; each
+reduction pass reads the state once. The state (2 GiB) is larger than L2
+(129 MB), so no flush is needed between iterations.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (the path does not shard:
+one state per GPU); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2308_01999_gb300 import inputs as gen  # noqa: E402
+
+N_QUBITS = 28
+DEPTH = 40
+AMP_BYTES = 8
+METRIC = "gate-apply HBM GB/s (28-qubit complex64 random circuit, unfused, one gate per launch)"
+UNIT = "GB/s"
+WORKLOAD = ("28-qubit random circuit, complex64 state (2 GiB) resident in HBM, depth 40: Haar SU(2) on all "
+            "qubits + CZ/CNOT/CRZ on 14 random disjoint pairs per layer, one gate per launch, then <Z_q> for all "
+            "28 qubits, 8 random Pauli strings and a 2-qubit parity measurement")
+FRACTION = {"su2": 1.0, "cnot": 0.5, "crz": 0.5, "cz": 0.25}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload():
+    gates = gen.circuit_config1(N_QUBITS, DEPTH, seed=1)
+    paulis, sites = gen.random_pauli_strings(N_QUBITS, 8, gen.rng_for(101))
+    return gates, paulis, sites
+
+
+def gate_bytes(g):
+    return FRACTION[g.name] * 2 * AMP_BYTES * (1 << N_QUBITS)
+
+
+def reduction_passes(paulis):
+    """Passes over the state: <Z_q> (x = 0, 8 strings per pass), the Pauli strings
+    grouped by their X/Y mask (8 per pass), and one parity pass."""
+    zpasses = (N_QUBITS + 7) // 8
+    xs = {}
+    for p in paulis:
+        x = 0
+        for q, c in enumerate(p):
+            if c in (1, 2):
+                x |= 1 << q
+        xs[x] = xs.get(x, 0) + 1
+    return zpasses + sum((c + 7) // 8 for c in xs.values()) + 1
+
+
+def step_bytes(gates, paulis):
+    return sum(gate_bytes(g) for g in gates) + reduction_passes(paulis) * AMP_BYTES * (1 << N_QUBITS)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (clocks and throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.dev = device_id
+        self.proc = None
+        self.path = os.path.join("/tmp", f"sv_bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        load = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id(torch, dev) -> str:
+    """nvidia-smi's name for the device (its UUID, independent of CUDA_VISIBLE_DEVICES)."""
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return "0"
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(gates, budget_s: float = 12.0):
+    """The CPU oracle (complex128, OpenMP) on the first gates of the same circuit
+    at the same size, until `budget_s` of CPU work; value in the metric's unit
+    (the complex64 workload's algorithmic bytes for those gates / time)."""
+    from oracle import oracle as orc
+    cores = orc.set_threads(0)
+    psi = orc.zero_state(N_QUBITS)
+    done, moved = 0, 0.0
+    t0 = time.perf_counter()
+    while done < len(gates) and (done < 3 or time.perf_counter() - t0 < budget_s):
+        orc.apply(psi, gates[done])
+        moved += gate_bytes(gates[done])
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": moved / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {done} of {len(gates)} gates of the same 28-qubit circuit, complex128 oracle "
+                      f"({cores} OpenMP threads), {dt:.1f} s; GB/s counts the complex64 workload's bytes"}
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores on the same workload,
+    each step a bounded sample (a fixed slice of the circuit's gates)."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    gates, _, _ = workload()
+    cores = orc.set_threads(0)
+    psi = orc.zero_state(N_QUBITS)
+    per_step = 4
+    pos = 0
+
+    def one_step():
+        nonlocal pos
+        moved = 0.0
+        for _ in range(per_step):
+            g = gates[pos % len(gates)]
+            orc.apply(psi, g)
+            moved += gate_bytes(g)
+            pos += 1
+        return moved
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    moved = sum(one_step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    value = moved / dt / 1e9
+    sample = (f"{per_step} consecutive gates per step of the 28-qubit circuit, complex128 oracle, "
+              f"{cores} OpenMP threads; GB/s counts the complex64 workload's bytes")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2308_01999_gb300 import sv
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gates, paulis, sites = workload()
+    nbytes = step_bytes(gates, paulis)
+    n_gates = len(gates)
+    stream = torch.cuda.Stream(dev)
+    psi = torch.zeros(1 << N_QUBITS, dtype=torch.complex64, device=dev)
+    s = sv.StateVector(psi, stream)
+    zp = np.full((N_QUBITS, 1), 3, np.int32)
+    zs = np.arange(N_QUBITS, dtype=np.int32)[:, None]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    su2_idx = [i for i, g in enumerate(gates) if g.name == "su2"]
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_gates)]
+          for _ in range(args.steps)]
+
+    def one_step(step_events=None):
+        for i, g in enumerate(gates):
+            if step_events is not None:
+                step_events[i][0].record(stream)
+            s.apply_gate(g)
+            if step_events is not None:
+                step_events[i][1].record(stream)
+        z = s.expectation_z_all()
+        e = s.expectation_pauli(paulis, sites)
+        p = s.measure_probs([0, N_QUBITS - 1])
+        return z, e, p
+
+    with torch.cuda.stream(stream):
+        s.set_basis_state(0)
+        for _ in range(args.warmup):
+            one_step()
+        torch.cuda.synchronize()
+        clocks = Clocks(gpu_id(torch, dev))
+        launches0 = s.launches()
+        per_gate_ms = {i: 0.0 for i in range(n_gates)}
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            one_step(ev[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        for k in range(args.steps):
+            for i in range(n_gates):
+                per_gate_ms[i] += ev[k][i][0].elapsed_time(ev[k][i][1])
+        ms = t0.elapsed_time(t1) / args.steps
+        launches = (s.launches() - launches0) // max(1, args.steps) * args.steps
+
+        # end to end through the C ABI with host buffers: pinned initial state in,
+        # final state out, every step
+        h_in = torch.zeros(1 << N_QUBITS, dtype=torch.complex64, pin_memory=True)
+        h_in[0] = 1
+        h_out = torch.empty(1 << N_QUBITS, dtype=torch.complex64, pin_memory=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_steps = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(e_steps):
+            sv.sv_copy_from_host(s.handle, h_in.data_ptr())
+            one_step()
+            sv.sv_copy_to_host(s.handle, h_out.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = e0.elapsed_time(e1) / e_steps
+
+    if world > 1:
+        t = torch.tensor([ms, e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peak, peak_kind = load_peaks()
+    su2_ms = [per_gate_ms[i] / args.steps for i in su2_idx]
+    su2_bytes = 2 * AMP_BYTES * (1 << N_QUBITS)
+    avg_su2 = sum(su2_ms) / len(su2_ms)
+    achieved = su2_bytes / (avg_su2 * 1e-3) / 1e9
+    per_q = {}
+    for i in su2_idx:
+        q = gates[i].targets[0]
+        per_q.setdefault(q, []).append(per_gate_ms[i] / args.steps)
+    per_target = {str(q): round(su2_bytes / (np.mean(v) * 1e-3) / 1e9, 1) for q, v in sorted(per_q.items())}
+    per_kind = {}
+    for kind in ("cz", "cnot", "crz"):
+        idx = [i for i, g in enumerate(gates) if g.name == kind]
+        if idx:
+            t = np.mean([per_gate_ms[i] / args.steps for i in idx])
+            per_kind[kind] = round(gate_bytes(gates[idx[0]]) / (t * 1e-3) / 1e9, 1)
+    gates_ms = sum(per_gate_ms.values()) / args.steps
+    value = world * nbytes / (ms * 1e-3) / 1e9
+    cpu = cpu_baseline(gates) if world == 1 and not args.no_cpu_baseline else None
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            traffic = json.load(f).get("k_dense_1q_per_launch_bytes")
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "depth": DEPTH, "gates_per_step": n_gates,
+                   "state_bytes": AMP_BYTES << N_QUBITS, "bytes_per_step": nbytes,
+                   "l2": "no flush: the 2 GiB state exceeds the 129 MB L2", "parallelism": f"replicas x{world}"},
+        "gates_per_s": round(world * n_gates / (gates_ms * 1e-3), 1),
+        "gate_time_ms_per_step": round(gates_ms, 3),
+        "roofline": {"bound": "hbm", "kernel": "k_dense (1-qubit dense, SU(2))", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "frac_of_8tbs": round(achieved / 8000.0, 4), "traffic": traffic,
+                     "algorithmic_bytes_per_launch": su2_bytes, "avg_launch_ms": round(avg_su2, 4)},
+        "per_target_gbs": per_target, "per_kind_gbs": per_kind,
+        "gpu_launches": int(launches),
+        "e2e": {"value": round(world * nbytes / (e2e_ms * 1e-3) / 1e9, 1), "unit": UNIT,
+                "h2d_bytes_per_step": AMP_BYTES << N_QUBITS, "d2h_bytes_per_step": AMP_BYTES << N_QUBITS,
+                "ms_per_step": round(e2e_ms, 3)},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--qubits", type=int, default=28,
+                    help="state size; 28 is the benchmark workload, smaller sizes are for profiling captures")
+    args = ap.parse_args()
+    global N_QUBITS
+    N_QUBITS = args.qubits
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

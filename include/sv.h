@@ -1,0 +1,192 @@
+/*
+ * sv.h -- C ABI of the GB300 state-vector simulator core (libsv.so).
+ *
+ * The library applies quantum gates to a state vector held in GPU memory and
+ * reduces measurement probabilities and Pauli-string expectation values, as
+ * the state-vector primitives of the cuQuantum paper describe them (arXiv
+ * 2308.01999, Sec. II-A, Table I; gate fusion Sec. II-B and Sec. II-D-1).
+ *
+ * Conventions (the paper fixes only that each index bit is one qubit, Sec. II-C):
+ *   - qubit q is bit q of the amplitude index (little-endian);
+ *   - a state of n qubits is 2^n amplitudes, interleaved (re, im):
+ *     SV_C64 = two floats (8 bytes), SV_C128 = two doubles (16 bytes);
+ *   - a gate matrix is HOST memory, row-major, 2^k x 2^k complex128 given as
+ *     interleaved (re, im) doubles; row/column index bit j belongs to targets[j];
+ *   - a controlled gate applies its matrix where every control qubit equals its
+ *     control value (all 1 when control_values is NULL), identity elsewhere.
+ *
+ * Memory ownership (Sec. II-A, "relaxed memory model" and "small memory
+ * footprint"): the state vector belongs to the caller, who allocates it in GPU
+ * memory; the library only borrows the pointer. Every operation runs in place.
+ * A handle owns one small device workspace (SV_WORKSPACE_BYTES) and one small
+ * pinned host buffer, allocated by sv_create and freed by sv_destroy. Host
+ * arrays passed to any call (matrices, qubit lists, Pauli strings) are read
+ * before the call returns and may be freed right after.
+ *
+ * Streams: work is enqueued on the handle's CUDA stream and returns without
+ * waiting, except the calls documented as synchronising (they return host
+ * values and wait for the stream).
+ *
+ * Errors: every call returns an sv_status_t; nothing is thrown across the ABI.
+ * A call that returns an error has enqueued no work, except SV_ERR_CUDA, which
+ * reports a failed CUDA call or launch (cudaGetLastError is cleared by then).
+ */
+#ifndef SV_GB300_SV_H
+#define SV_GB300_SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SV_API __attribute__((visibility("default")))
+#else
+#define SV_API
+#endif
+
+#define SV_MAX_TARGETS 6         /* largest dense gate, 64 x 64 */
+#define SV_MAX_CONTROLS 24       /* control qubits of one gate */
+#define SV_MAX_QUBITS 36         /* 2^36 c64 amplitudes = 512 GiB: beyond one GPU */
+#define SV_WORKSPACE_BYTES (32u << 20)  /* device workspace per handle ("a few tens of MB", Table I) */
+
+typedef struct sv_ctx *sv_handle_t;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype_t;
+
+typedef enum {
+    SV_OK = 0,
+    SV_ERR_INVALID_ARGUMENT = 1,    /* bad qubit index, duplicate qubit, k out of range, NULL pointer */
+    SV_ERR_NOT_SUPPORTED = 2,       /* e.g. tensor-core precision on a complex128 state */
+    SV_ERR_INSUFFICIENT_WORKSPACE = 3,
+    SV_ERR_CUDA = 4,                /* a CUDA call or kernel launch failed */
+    SV_ERR_TIMEOUT = 5,             /* a bounded device-side wait gave up (see sv_check_device_status) */
+    SV_ERR_ALLOC = 6                /* the handle's workspace could not be allocated */
+} sv_status_t;
+
+/* Arithmetic of fused gates of 5-6 qubits on a complex64 state (Sec. II-B).
+ * NATIVE: FP32 complex arithmetic on CUDA cores.
+ * TF32: tensor cores, operands rounded to TF32, FP32 accumulation.
+ * SPLIT_BF16: tensor cores, each operand split into a BF16 high and low part,
+ *   three products (hi*hi + hi*lo + lo*hi), FP32 accumulation. */
+typedef enum { SV_PREC_NATIVE = 0, SV_PREC_TF32 = 1, SV_PREC_SPLIT_BF16 = 2 } sv_precision_t;
+
+typedef enum { SV_PAULI_I = 0, SV_PAULI_X = 1, SV_PAULI_Y = 2, SV_PAULI_Z = 3 } sv_pauli_t;
+
+/* One gate of a circuit, as sv_apply_fused and sv_fuse_plan read it. */
+typedef struct {
+    int n_targets;                        /* 1..SV_MAX_TARGETS */
+    int targets[SV_MAX_TARGETS];
+    int n_controls;                       /* 0..SV_MAX_CONTROLS */
+    int controls[SV_MAX_CONTROLS];
+    int control_values[SV_MAX_CONTROLS];  /* each 0 or 1 */
+    const double *matrix;                 /* host, row-major 2^k x 2^k complex128 (re, im) */
+} sv_gate_t;
+
+/* Create a handle for an n-qubit state of the given dtype at d_state (device
+ * memory, 2^n amplitudes, at least 16-byte aligned, owned by the caller).
+ * stream: a cudaStream_t (NULL = the legacy default stream). Allocates the
+ * handle's workspace on the current device. The state's contents are not
+ * touched. Errors: INVALID_ARGUMENT (n outside 1..SV_MAX_QUBITS, NULL pointers,
+ * misaligned d_state), ALLOC, CUDA. (Table I, "Resource management".) */
+SV_API sv_status_t sv_create(int n_qubits, sv_dtype_t dtype, void *d_state, void *stream, sv_handle_t *out);
+
+/* Wait for the handle's stream, then free the workspace; never frees the state. */
+SV_API sv_status_t sv_destroy(sv_handle_t h);
+
+/* Enqueue later work on another stream (a cudaStream_t). */
+SV_API sv_status_t sv_set_stream(sv_handle_t h, void *stream);
+
+/* Point the handle at another state of the same size and dtype. */
+SV_API sv_status_t sv_set_state_pointer(sv_handle_t h, void *d_state);
+
+/* psi <- |index> (one amplitude 1, the rest 0). Asynchronous. */
+SV_API sv_status_t sv_set_basis_state(sv_handle_t h, uint64_t index);
+
+/* Accessor (Table I) without qubit reordering: copy the whole state between a
+ * host buffer of 2^n amplitudes and the device. Pinned host memory makes the
+ * copy faster. Both synchronise the stream before returning. */
+SV_API sv_status_t sv_copy_from_host(sv_handle_t h, const void *host);
+SV_API sv_status_t sv_copy_to_host(sv_handle_t h, void *host);
+
+/* Gate application (Table I; Sec. II-B): psi <- G psi with G the 2^k x 2^k
+ * matrix on targets (k = n_targets, 1..6), applied where the controls hold.
+ * adjoint != 0 applies the conjugate transpose. The library inspects the
+ * matrix exactly (no tolerance) and takes the cheapest exact form: target
+ * bits on which the matrix is the identity in one half become controls, a
+ * diagonal matrix scales only the amplitudes it changes, and a generalized
+ * permutation matrix (one nonzero per row and column, e.g. X, CNOT) moves
+ * amplitudes without a matrix product (Sec. II-D-1). Asynchronous.
+ * Errors: INVALID_ARGUMENT for a qubit outside [0, n), a qubit listed twice
+ * (among targets and controls together), k outside 1..6, more than
+ * SV_MAX_CONTROLS controls, a control value other than 0/1, NULL pointers. */
+SV_API sv_status_t sv_apply_matrix(sv_handle_t h, const int *targets, int n_targets,
+                            const int *controls, const int *control_values, int n_controls,
+                            const double *matrix, int adjoint);
+
+/* Gate fusion (Sec. II-B; qsim's max_fused_gate_size, Sec. II-D-1): the gates
+ * are grouped greedily, in program order and moving a gate only past gates on
+ * disjoint qubits, into blocks of at most max_fused_qubits qubits (1..6); each
+ * block's matrix is composed on the host in FP64 and applied once. Blocks of
+ * 5-6 qubits run in `prec` (tensor cores for TF32 / SPLIT_BF16), smaller ones
+ * in native precision. *n_fused_out (may be NULL) receives the block count.
+ * Asynchronous. Errors: as sv_apply_matrix for each gate; NOT_SUPPORTED for a
+ * tensor-core precision on a complex128 state. */
+SV_API sv_status_t sv_apply_fused(sv_handle_t h, const sv_gate_t *gates, int n_gates,
+                           int max_fused_qubits, sv_precision_t prec, int *n_fused_out);
+
+/* Host-only view of the fusion pass, for inspection and tests (no GPU needed).
+ * Writes at most max_blocks blocks: block b acts on block_k[b] qubits
+ * block_targets[6*b .. 6*b+k-1] (bit j of its matrix index is target j) with
+ * the 2^k x 2^k complex128 matrix at block_matrices + b * 64*64*2 doubles
+ * (row-major, leading dimension 2^k). Blocks are applied in order.
+ * Errors: INVALID_ARGUMENT; INSUFFICIENT_WORKSPACE if more than max_blocks. */
+SV_API sv_status_t sv_fuse_plan(const sv_gate_t *gates, int n_gates, int n_qubits, int max_fused_qubits,
+                         int max_blocks, int *n_blocks_out, int *block_k, int *block_targets,
+                         double *block_matrices);
+
+/* Pauli-string expectation values (Table I, "Expectation"):
+ * out[s] = Re <psi| P_s |psi>, P_s = prod_i paulis[s*n_sites + i] on qubit
+ * sites[s*n_sites + i]. Not divided by <psi|psi>. Products are formed in the
+ * state's precision and accumulated in FP64. out is host memory of n_strings
+ * doubles. Synchronises the stream. Errors: INVALID_ARGUMENT for a site outside
+ * [0, n), a site repeated within a string, a code outside 0..3. */
+SV_API sv_status_t sv_expectation_pauli(sv_handle_t h, const int *paulis, const int *sites,
+                                 int n_sites, int n_strings, double *out);
+
+/* Probabilities of a measurement in the Z-product basis of `qubits` (Table I,
+ * "Measurement"): p_even/p_odd = sum of |psi_i|^2 over basis states whose
+ * measured bits have even/odd parity, in FP64. Synchronises the stream. */
+SV_API sv_status_t sv_measure_probs(sv_handle_t h, const int *qubits, int n_qubits,
+                             double *p_even, double *p_odd);
+
+/* Collapse onto one parity outcome (Table I: collapse is separate from the
+ * probability computation): amplitudes of the other parity become 0, the rest
+ * are scaled by 1/sqrt(prob). Asynchronous. INVALID_ARGUMENT unless prob > 0. */
+SV_API sv_status_t sv_collapse(sv_handle_t h, const int *qubits, int n_qubits, int parity, double prob);
+
+/* Measurement: parity 0 iff randnum < p_even / (p_even + p_odd); with collapse
+ * != 0 the state collapses onto that outcome. randnum in [0, 1). Synchronises. */
+SV_API sv_status_t sv_measure(sv_handle_t h, const int *qubits, int n_qubits, double randnum,
+                       int collapse, int *parity_out);
+
+/* <psi|psi> in FP64. Synchronises the stream. */
+SV_API sv_status_t sv_norm2(sv_handle_t h, double *out);
+
+/* Synchronise the stream and report whether a bounded device-side wait gave
+ * up since the last call (SV_ERR_TIMEOUT), then clear the flag. */
+SV_API sv_status_t sv_check_device_status(sv_handle_t h);
+
+/* Number of kernels this handle has launched since sv_create. */
+SV_API sv_status_t sv_launch_count(sv_handle_t h, uint64_t *out);
+
+/* A static description of a status code. */
+SV_API const char *sv_status_string(sv_status_t s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SV_GB300_SV_H */

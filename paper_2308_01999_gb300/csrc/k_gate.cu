@@ -1,0 +1,486 @@
+// k_gate.cu -- gate application on CUDA cores (Table I, "Gate application";
+// Sec. II-B: gate application is memory-bound for small k, so every kernel here
+// is a single streaming pass that reads and writes each touched amplitude once).
+//
+// Three kernel families, all in place:
+//   k_dense      dense 2^k x 2^k product per group, k <= 4, group data in registers;
+//   k_dense_smem dense product for any k <= 6, a tile of groups staged in shared memory
+//                (for k = 5, 6 the work is ALU-bound on CUDA cores; the tensor-core
+//                path in k_tc.cu is the fast one);
+//   k_diag       diagonal matrix on the amplitudes where the controls hold;
+//   k_perm       generalized permutation matrix (one nonzero per row/column).
+//
+// Vector access. A complex64 amplitude is 8 bytes; every access is 16 bytes wide
+// where the index layout allows it:
+//   PAIR   bit 0 is neither a target nor a control: groups g and g+1 start at
+//          adjacent amplitudes, so one float4 holds member j of both groups;
+//   T0     bit 0 is the lowest target: members 2m and 2m+1 of a group are
+//          adjacent, so one float4 holds both;
+//   SCALAR one amplitude per access (complex128: always 16 bytes; complex64 with a
+//          control on bit 0: 8 bytes).
+// Within a warp, consecutive threads take consecutive units, so for every member
+// the warp reads one contiguous run (coalesced), also for high target qubits.
+#include <vector>
+
+#include "sv_internal.h"
+
+namespace svk {
+namespace {
+
+enum Mode { PAIR = 0, T0 = 1, SCALAR = 2 };
+constexpr int kThreads = 256;
+
+template <typename R> struct CT;
+template <> struct CT<float> { using T = float2; };
+template <> struct CT<double> { using T = double2; };
+
+__device__ __forceinline__ float fmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmac(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// acc += m * v (complex)
+template <typename C>
+__device__ __forceinline__ void cmad(C &acc, const C &m, const C &v) {
+    acc.x = fmac(m.x, v.x, acc.x);
+    acc.x = fmac(-m.y, v.y, acc.x);
+    acc.y = fmac(m.x, v.y, acc.y);
+    acc.y = fmac(m.y, v.x, acc.y);
+}
+
+template <typename C>
+__device__ __forceinline__ C cmul(const C &a, const C &b) {
+    C r;
+    r.x = fmac(a.x, b.x, -a.y * b.y);
+    r.y = fmac(a.x, b.y, a.y * b.x);
+    return r;
+}
+
+// Zero bits inserted at G.pos (ascending), then the control bits set.
+__device__ __forceinline__ uint64_t insert_zeros(uint64_t g, const GroupGeom &G) {
+#pragma unroll 1
+    for (int i = 0; i < G.ns; ++i) {
+        const uint64_t lo = g & ((1ull << G.pos[i]) - 1ull);
+        g = ((g ^ lo) << 1) | lo;
+    }
+    return g | G.cset;
+}
+
+__device__ __forceinline__ float4 ld16(const float2 *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st16(float2 *p, const float4 &v) { *reinterpret_cast<float4 *>(p) = v; }
+
+template <int K> struct Offs { uint64_t o[1 << K]; };
+template <typename R, int K> struct MatK { typename CT<R>::T m[1 << (2 * K)]; };
+
+// ---------------------------------------------------------------------------
+// dense, k <= 4, registers
+// ---------------------------------------------------------------------------
+template <typename R, int K, int MODE, int U>
+__global__ void __launch_bounds__(kThreads)
+k_dense(typename CT<R>::T *__restrict__ sv, uint64_t n_units, GroupGeom G, Offs<K> O, MatK<R, K> M) {
+    using C = typename CT<R>::T;
+    constexpr int D = 1 << K;
+    constexpr int E = (MODE == PAIR) ? 2 : 1;
+    const uint64_t u0 = (uint64_t)blockIdx.x * (kThreads * U) + threadIdx.x;
+    C v[U][D][E];
+    uint64_t base[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint64_t unit = u0 + (uint64_t)u * kThreads;
+        base[u] = insert_zeros(MODE == PAIR ? (unit << 1) : unit, G);
+        if (unit < n_units) {
+            if constexpr (MODE == PAIR) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const float4 f = ld16(reinterpret_cast<const float2 *>(sv) + base[u] + O.o[j]);
+                    v[u][j][0] = C{f.x, f.y};
+                    v[u][j][E - 1] = C{f.z, f.w};
+                }
+            } else if constexpr (MODE == T0) {
+#pragma unroll
+                for (int m = 0; m < D / 2; ++m) {
+                    const float4 f = ld16(reinterpret_cast<const float2 *>(sv) + base[u] + O.o[2 * m]);
+                    v[u][2 * m][0] = C{f.x, f.y};
+                    v[u][2 * m + 1][0] = C{f.z, f.w};
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < D; ++j) v[u][j][0] = sv[base[u] + O.o[j]];
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint64_t unit = u0 + (uint64_t)u * kThreads;
+        if (unit >= n_units) continue;
+        C w[D][E];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                C acc{0, 0};
+#pragma unroll
+                for (int l = 0; l < D; ++l) cmad(acc, M.m[j * D + l], v[u][l][e]);
+                w[j][e] = acc;
+            }
+        }
+        if constexpr (MODE == PAIR) {
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+                st16(reinterpret_cast<float2 *>(sv) + base[u] + O.o[j],
+                     make_float4(w[j][0].x, w[j][0].y, w[j][E - 1].x, w[j][E - 1].y));
+        } else if constexpr (MODE == T0) {
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m)
+                st16(reinterpret_cast<float2 *>(sv) + base[u] + O.o[2 * m],
+                     make_float4(w[2 * m][0].x, w[2 * m][0].y, w[2 * m + 1][0].x, w[2 * m + 1][0].y));
+        } else {
+#pragma unroll
+            for (int j = 0; j < D; ++j) sv[base[u] + O.o[j]] = w[j][0];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// dense, any k <= 6, tile of 2048 amplitudes in shared memory, persistent grid
+// ---------------------------------------------------------------------------
+constexpr int kTile = 2048;
+
+template <typename R, int K>
+__global__ void __launch_bounds__(kThreads)
+k_dense_smem(typename CT<R>::T *__restrict__ sv, uint64_t n_groups, GroupGeom G, Offs<K> O,
+             const typename CT<R>::T *__restrict__ Mg) {
+    using C = typename CT<R>::T;
+    constexpr int D = 1 << K;
+    constexpr int GB = kTile / D;          // groups per tile (>= 32)
+    constexpr int PER = kTile / kThreads;  // amplitudes per thread
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *Ms = reinterpret_cast<C *>(smem_raw);
+    C *Ts = Ms + D * D;
+    for (int i = threadIdx.x; i < D * D; i += kThreads) Ms[i] = Mg[i];
+    const uint64_t n_tiles = (n_groups + GB - 1) / GB;
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        uint64_t addr[PER];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int idx = threadIdx.x + r * kThreads;
+            const int j = idx / GB, g = idx % GB;
+            const uint64_t gg = tile * GB + g;
+            addr[r] = insert_zeros(gg, G) + O.o[j];
+            if (gg < n_groups) Ts[idx] = sv[addr[r]];
+        }
+        __syncthreads();
+        C out[PER];
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int idx = threadIdx.x + r * kThreads;
+            const int j = idx / GB, g = idx % GB;
+            C acc{0, 0};
+#pragma unroll 8
+            for (int l = 0; l < D; ++l) cmad(acc, Ms[j * D + l], Ts[l * GB + g]);
+            out[r] = acc;
+        }
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int idx = threadIdx.x + r * kThreads;
+            if (tile * GB + (idx % GB) < n_groups) sv[addr[r]] = out[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// diagonal on targets where the controls hold (k = 0 is a phase on a subspace)
+// ---------------------------------------------------------------------------
+template <typename R> struct DiagP {
+    typename CT<R>::T d[1 << SV_MAX_TARGETS];
+    int tpos[SV_MAX_TARGETS];
+    int k;
+};
+
+template <typename C, typename P>
+__device__ __forceinline__ C diag_scale(const C &a, uint64_t idx, const P &p) {
+    int j = 0;
+#pragma unroll 1
+    for (int t = 0; t < p.k; ++t) j |= (int)((idx >> p.tpos[t]) & 1u) << t;
+    return cmul(p.d[j], a);
+}
+
+template <typename R, int MODE, int U>
+__global__ void __launch_bounds__(kThreads)
+k_diag(typename CT<R>::T *__restrict__ sv, uint64_t n_units, GroupGeom G, DiagP<R> P) {
+    using C = typename CT<R>::T;
+    const uint64_t u0 = (uint64_t)blockIdx.x * (kThreads * U) + threadIdx.x;
+    if constexpr (MODE == PAIR) {
+        float4 f[U];
+        uint64_t idx[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t unit = u0 + (uint64_t)u * kThreads;
+            idx[u] = insert_zeros(unit << 1, G);
+            if (unit < n_units) f[u] = ld16(reinterpret_cast<const float2 *>(sv) + idx[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (u0 + (uint64_t)u * kThreads >= n_units) continue;
+            const C a = diag_scale(C{f[u].x, f[u].y}, idx[u], P);
+            const C b = diag_scale(C{f[u].z, f[u].w}, idx[u] + 1, P);
+            st16(reinterpret_cast<float2 *>(sv) + idx[u], make_float4(a.x, a.y, b.x, b.y));
+        }
+    } else {
+        C a[U];
+        uint64_t idx[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t unit = u0 + (uint64_t)u * kThreads;
+            idx[u] = insert_zeros(unit, G);
+            if (unit < n_units) a[u] = sv[idx[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (u0 + (uint64_t)u * kThreads >= n_units) continue;
+            sv[idx[u]] = diag_scale(a[u], idx[u], P);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// generalized permutation: out[j] = d[j] * in[perm[j]]; source l goes to
+// destination pinv[l] with factor d[pinv[l]] (both precomputed on the host)
+// ---------------------------------------------------------------------------
+template <typename R, int K> struct PermP {
+    typename CT<R>::T f[1 << K];   // factor applied to source member l
+    uint64_t dst[1 << K];          // offset of the destination of source member l
+    uint64_t src[1 << K];          // offset of source member l
+};
+
+template <typename R, int K, int MODE, int U>
+__global__ void __launch_bounds__(kThreads)
+k_perm(typename CT<R>::T *__restrict__ sv, uint64_t n_units, GroupGeom G, PermP<R, K> P) {
+    using C = typename CT<R>::T;
+    constexpr int D = 1 << K;
+    constexpr int E = (MODE == PAIR) ? 2 : 1;
+    const uint64_t u0 = (uint64_t)blockIdx.x * (kThreads * U) + threadIdx.x;
+    C v[U][D][E];
+    uint64_t base[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint64_t unit = u0 + (uint64_t)u * kThreads;
+        base[u] = insert_zeros(MODE == PAIR ? (unit << 1) : unit, G);
+        if (unit < n_units) {
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                if constexpr (MODE == PAIR) {
+                    const float4 f = ld16(reinterpret_cast<const float2 *>(sv) + base[u] + P.src[l]);
+                    v[u][l][0] = C{f.x, f.y};
+                    v[u][l][E - 1] = C{f.z, f.w};
+                } else {
+                    v[u][l][0] = sv[base[u] + P.src[l]];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (u0 + (uint64_t)u * kThreads >= n_units) continue;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            const C a = cmul(P.f[l], v[u][l][0]);
+            if constexpr (MODE == PAIR) {
+                const C b = cmul(P.f[l], v[u][l][E - 1]);
+                st16(reinterpret_cast<float2 *>(sv) + base[u] + P.dst[l], make_float4(a.x, a.y, b.x, b.y));
+            } else {
+                sv[base[u] + P.dst[l]] = a;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <typename C> C to_c(const double *z) { return C{(decltype(C{}.x))z[0], (decltype(C{}.x))z[1]}; }
+
+inline unsigned grid_for(uint64_t units, int per_block) {
+    const uint64_t b = (units + per_block - 1) / per_block;
+    return (unsigned)(b == 0 ? 1 : b);
+}
+
+// bytes in flight per thread are kept near 64-128 B
+template <typename R, int K, int MODE> constexpr int dense_u() {
+    constexpr int unit_bytes = (MODE == PAIR ? 16 : (int)sizeof(typename CT<R>::T)) * (1 << K) / (MODE == T0 ? 2 : 1);
+    return unit_bytes >= 128 ? 1 : (unit_bytes >= 64 ? 2 : 4);
+}
+
+template <typename R, int K, int MODE>
+cudaError_t run_dense_reg(const LaunchCtx &L, void *sv, uint64_t n_units, const GroupGeom &G, const Offs<K> &O,
+                          const MatK<R, K> &M) {
+    constexpr int U = dense_u<R, K, MODE>();
+    k_dense<R, K, MODE, U><<<grid_for(n_units, kThreads * U), kThreads, 0, L.stream>>>(
+        reinterpret_cast<typename CT<R>::T *>(sv), n_units, G, O, M);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+template <typename R, int K>
+cudaError_t dense_reg(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, const double *mat) {
+    using C = typename CT<R>::T;
+    constexpr int D = 1 << K;
+    Offs<K> O;
+    for (int j = 0; j < D; ++j) {
+        uint64_t o = 0;
+        for (int t = 0; t < K; ++t)
+            if ((j >> t) & 1) o |= 1ull << tpos[t];
+        O.o[j] = o;
+    }
+    MatK<R, K> M;
+    for (int i = 0; i < D * D; ++i) M.m[i] = to_c<C>(mat + 2 * i);
+    const uint64_t n_groups = 1ull << (n - G.ns);
+    const bool bit0_special = G.ns > 0 && G.pos[0] == 0;
+    if constexpr (sizeof(R) == 4) {
+        if (!bit0_special && n_groups >= 2) return run_dense_reg<R, K, PAIR>(L, sv, n_groups / 2, G, O, M);
+        if (tpos[0] == 0) return run_dense_reg<R, K, T0>(L, sv, n_groups, G, O, M);
+    }
+    return run_dense_reg<R, K, SCALAR>(L, sv, n_groups, G, O, M);
+}
+
+template <typename R, int K>
+cudaError_t dense_smem(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, const double *mat,
+                       void *d_mat) {
+    using C = typename CT<R>::T;
+    constexpr int D = 1 << K;
+    Offs<K> O;
+    for (int j = 0; j < D; ++j) {
+        uint64_t o = 0;
+        for (int t = 0; t < K; ++t)
+            if ((j >> t) & 1) o |= 1ull << tpos[t];
+        O.o[j] = o;
+    }
+    std::vector<C> hm(D * D);
+    for (int i = 0; i < D * D; ++i) hm[i] = to_c<C>(mat + 2 * i);
+    cudaError_t e = cudaMemcpyAsync(d_mat, hm.data(), sizeof(C) * D * D, cudaMemcpyHostToDevice, L.stream);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(C) * (D * D + kTile);
+    auto kern = k_dense_smem<R, K>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t n_groups = 1ull << (n - G.ns);
+    const uint64_t n_tiles = (n_groups + kTile / D - 1) / (kTile / D);
+    uint64_t grid = (uint64_t)L.num_sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > n_tiles) grid = n_tiles;
+    kern<<<(unsigned)grid, kThreads, smem, L.stream>>>(reinterpret_cast<C *>(sv), n_groups, G, O,
+                                                       reinterpret_cast<const C *>(d_mat));
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t dense_any(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, int k,
+                      const double *mat, void *d_mat) {
+    switch (k) {
+    case 1: return dense_reg<R, 1>(L, sv, n, G, tpos, mat);
+    case 2: return dense_reg<R, 2>(L, sv, n, G, tpos, mat);
+    case 3: return dense_reg<R, 3>(L, sv, n, G, tpos, mat);
+    case 4: return dense_reg<R, 4>(L, sv, n, G, tpos, mat);
+    case 5: return dense_smem<R, 5>(L, sv, n, G, tpos, mat, d_mat);
+    case 6: return dense_smem<R, 6>(L, sv, n, G, tpos, mat, d_mat);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R>
+cudaError_t diag_any(const LaunchCtx &L, void *sv, int n, const GroupGeom &Gc, const int *tpos, int k,
+                     const double *diag) {
+    using C = typename CT<R>::T;
+    DiagP<R> P;
+    P.k = k;
+    for (int t = 0; t < SV_MAX_TARGETS; ++t) P.tpos[t] = t < k ? tpos[t] : 0;
+    for (int j = 0; j < (1 << SV_MAX_TARGETS); ++j) P.d[j] = j < (1 << k) ? to_c<C>(diag + 2 * j) : C{1, 0};
+    const uint64_t n_amps = 1ull << (n - Gc.ns);
+    const bool bit0_ctl = Gc.ns > 0 && Gc.pos[0] == 0;
+    constexpr int U = 4;
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+        if (!bit0_ctl && n_amps >= 2) {
+            k_diag<R, PAIR, U><<<grid_for(n_amps / 2, kThreads * U), kThreads, 0, L.stream>>>(
+                reinterpret_cast<C *>(sv), n_amps / 2, Gc, P);
+            done = true;
+        }
+    }
+    if (!done)
+        k_diag<R, SCALAR, U><<<grid_for(n_amps, kThreads * U), kThreads, 0, L.stream>>>(
+            reinterpret_cast<C *>(sv), n_amps, Gc, P);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+template <typename R, int K>
+cudaError_t perm_k(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, const int *perm,
+                   const double *d) {
+    using C = typename CT<R>::T;
+    constexpr int D = 1 << K;
+    auto off = [&](int j) {
+        uint64_t o = 0;
+        for (int t = 0; t < K; ++t)
+            if ((j >> t) & 1) o |= 1ull << tpos[t];
+        return o;
+    };
+    PermP<R, K> P;
+    for (int j = 0; j < D; ++j) {
+        const int l = perm[j];           // out[j] = d[j] * in[l]
+        P.src[l] = off(l);
+        P.dst[l] = off(j);
+        P.f[l] = to_c<C>(d + 2 * j);
+    }
+    const uint64_t n_groups = 1ull << (n - G.ns);
+    const bool bit0_special = G.ns > 0 && G.pos[0] == 0;
+    constexpr int U = (K <= 2) ? 2 : 1;
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+        if (!bit0_special && n_groups >= 2) {
+            k_perm<R, K, PAIR, U><<<grid_for(n_groups / 2, kThreads * U), kThreads, 0, L.stream>>>(
+                reinterpret_cast<C *>(sv), n_groups / 2, G, P);
+            done = true;
+        }
+    }
+    if (!done)
+        k_perm<R, K, SCALAR, U><<<grid_for(n_groups, kThreads * U), kThreads, 0, L.stream>>>(
+            reinterpret_cast<C *>(sv), n_groups, G, P);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t perm_any(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, int k, const int *perm,
+                     const double *d) {
+    switch (k) {
+    case 1: return perm_k<R, 1>(L, sv, n, G, tpos, perm, d);
+    case 2: return perm_k<R, 2>(L, sv, n, G, tpos, perm, d);
+    case 3: return perm_k<R, 3>(L, sv, n, G, tpos, perm, d);
+    case 4: return perm_k<R, 4>(L, sv, n, G, tpos, perm, d);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_dense(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, const GroupGeom &G, const int *tpos,
+                         int k, const double *mat, void *d_mat) {
+    return dt == SV_C64 ? dense_any<float>(L, sv, n, G, tpos, k, mat, d_mat)
+                        : dense_any<double>(L, sv, n, G, tpos, k, mat, d_mat);
+}
+
+cudaError_t launch_diag(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, const GroupGeom &Gctl, const int *tpos,
+                        int k, const double *diag) {
+    return dt == SV_C64 ? diag_any<float>(L, sv, n, Gctl, tpos, k, diag)
+                        : diag_any<double>(L, sv, n, Gctl, tpos, k, diag);
+}
+
+cudaError_t launch_perm(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, const GroupGeom &G, const int *tpos,
+                        int k, const int *perm, const double *d) {
+    return dt == SV_C64 ? perm_any<float>(L, sv, n, G, tpos, k, perm, d)
+                        : perm_any<double>(L, sv, n, G, tpos, k, perm, d);
+}
+
+}  // namespace svk

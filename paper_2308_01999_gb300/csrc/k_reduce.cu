@@ -1,0 +1,324 @@
+// k_reduce.cu -- reductions over the state vector: Pauli-string expectation
+// values (Table I, "Expectation"), parity probabilities of a Z-product-basis
+// measurement and its collapse (Table I, "Measurement"), and the norm.
+//
+// Pauli expectation. For P = prod of Paulis, with x = mask of X/Y sites,
+// z = mask of Z/Y sites and nY = number of Y sites,
+//   P|i> = i^{nY} (-1)^{popcount(i & z)} |i ^ x>,
+//   <psi|P|psi> = sum_i i^{nY} (-1)^{popcount(i & z)} psi_i conj(psi_{i^x}),
+// which is real because P is Hermitian. With w_i = psi_i conj(psi_{i^x}) the
+// real part per term is +-Re(w_i) (nY even) or +-Im(w_i) (nY odd); the host
+// folds i^{nY} into a per-string selector and sign. Strings with the same x
+// share one pass: each pass reads every amplitude once, pairing unit i with
+// unit i ^ x so that both partners come from the same two loads.
+//
+// Precision. Terms are formed in the state's precision. For complex64 each
+// thread sums the terms of one loop iteration in FP32 (at most 16 terms per
+// string: 4 work items x 2 units x 2 amplitudes), so that partial carries a
+// relative rounding error of at most 16 u (u = 2^-24) of the sum of its terms'
+// magnitudes; partials are then summed in FP64 across iterations, threads and
+// blocks. Since sum_i |w_i| <= <psi|psi>, the absolute error of a complex64
+// expectation value is at most about 1e-6 <psi|psi> (typically far less).
+// complex128 uses FP64 throughout. Block partials are reduced by a
+// second kernel in a fixed order, so results are bitwise reproducible for a
+// given launch shape.
+#include "sv_internal.h"
+
+namespace svk {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kIlp = 4;     // work items loaded before any is consumed
+constexpr int kRun = 1;     // loop iterations summed in FP32 before an FP64 add
+
+template <typename R> struct CT;
+template <> struct CT<float> { using T = float2; static constexpr int V = 2; };
+template <> struct CT<double> { using T = double2; static constexpr int V = 1; };
+
+// V consecutive amplitudes starting at unit index u (16-byte load either way)
+template <typename R>
+__device__ __forceinline__ void load_unit(const typename CT<R>::T *sv, uint64_t u, typename CT<R>::T (&a)[CT<R>::V]) {
+    if constexpr (CT<R>::V == 2) {
+        const float4 f = reinterpret_cast<const float4 *>(sv)[u];
+        a[0] = float2{f.x, f.y};
+        a[1] = float2{f.z, f.w};
+    } else {
+        a[0] = sv[u];
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ C mul_conj(const C &a, const C &b) {  // a * conj(b)
+    C r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.y * b.x - a.x * b.y;
+    return r;
+}
+
+__device__ __forceinline__ uint64_t insert_zero(uint64_t g, int b) {
+    const uint64_t lo = g & ((1ull << b) - 1ull);
+    return ((g ^ lo) << 1) | lo;
+}
+
+template <int S>
+__device__ __forceinline__ void block_reduce_store(double (&v)[S], int nS, double *out) {
+    __shared__ double red[kThreads / 32][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        double x = v[s];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][s] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < nS) {
+        double acc = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) acc += red[w][threadIdx.x];
+        out[threadIdx.x] = acc;
+    }
+}
+
+// partials[b * 8 + s] summed over b in a fixed order; out[s] = sign[s] * sum
+__global__ void __launch_bounds__(kThreads)
+k_finish(const double *__restrict__ partials, int nblocks, int S, PauliPass P, int use_sign, double *__restrict__ out) {
+    __shared__ double red[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int s = 0; s < S; ++s) {
+        double x = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += kThreads) x += partials[(size_t)b * 8 + s];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double acc = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) acc += red[w];
+            out[s] = use_sign ? P.sign[s] * acc : acc;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_pauli(const typename CT<R>::T *__restrict__ sv, uint64_t n_work, int pair_bit, uint64_t xu, unsigned xl,
+        PauliPass P, double *__restrict__ partials) {
+    using C = typename CT<R>::T;
+    constexpr int V = CT<R>::V;
+    double tot[kPauliMaxS];
+    R run[kPauliMaxS];
+#pragma unroll
+    for (int s = 0; s < kPauliMaxS; ++s) { tot[s] = 0.0; run[s] = R(0); }
+    auto add = [&](uint64_t i, const C &w) {
+#pragma unroll
+        for (int s = 0; s < kPauliMaxS; ++s) {
+            if (s < P.S) {
+                const R t = P.use_im[s] ? w.y : w.x;
+                run[s] += (__popcll(i & P.z[s]) & 1) ? -t : t;
+            }
+        }
+    };
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads * kIlp;
+    int iter = 0;
+    for (uint64_t w0 = (uint64_t)blockIdx.x * kThreads * kIlp + threadIdx.x; w0 < n_work; w0 += stride) {
+        C A[kIlp][V], B[kIlp][V];
+        uint64_t ua[kIlp], ub[kIlp];
+#pragma unroll
+        for (int q = 0; q < kIlp; ++q) {
+            const uint64_t w = w0 + (uint64_t)q * kThreads;
+            ua[q] = pair_bit < 0 ? w : insert_zero(w, pair_bit);
+            ub[q] = ua[q] ^ xu;
+            if (w < n_work) {
+                load_unit<R>(sv, ua[q], A[q]);
+                if (pair_bit >= 0) load_unit<R>(sv, ub[q], B[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kIlp; ++q) {
+            if (w0 + (uint64_t)q * kThreads >= n_work) continue;
+            if (pair_bit < 0) {
+#pragma unroll
+                for (int e = 0; e < V; ++e) add(ua[q] * V + e, mul_conj(A[q][e], xl ? A[q][V - 1 - e] : A[q][e]));
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    // partner of element e is element e ^ xl of the other unit (xl is 0 or 1)
+                    add(ua[q] * V + e, mul_conj(A[q][e], xl ? B[q][V - 1 - e] : B[q][e]));
+                    add(ub[q] * V + e, mul_conj(B[q][e], xl ? A[q][V - 1 - e] : A[q][e]));
+                }
+            }
+        }
+        if (++iter == kRun) {
+#pragma unroll
+            for (int s = 0; s < kPauliMaxS; ++s) { tot[s] += (double)run[s]; run[s] = R(0); }
+            iter = 0;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < kPauliMaxS; ++s) tot[s] += (double)run[s];
+    block_reduce_store<kPauliMaxS>(tot, P.S, partials + (size_t)blockIdx.x * 8);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_parity(const typename CT<R>::T *__restrict__ sv, uint64_t n_units, uint64_t mask, double *__restrict__ partials) {
+    using C = typename CT<R>::T;
+    constexpr int V = CT<R>::V;
+    double tot[2] = {0.0, 0.0};
+    R run[2] = {R(0), R(0)};
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads * kIlp;
+    int iter = 0;
+    for (uint64_t u0 = (uint64_t)blockIdx.x * kThreads * kIlp + threadIdx.x; u0 < n_units; u0 += stride) {
+        C A[kIlp][V];
+#pragma unroll
+        for (int q = 0; q < kIlp; ++q)
+            if (u0 + (uint64_t)q * kThreads < n_units) load_unit<R>(sv, u0 + (uint64_t)q * kThreads, A[q]);
+#pragma unroll
+        for (int q = 0; q < kIlp; ++q) {
+            const uint64_t u = u0 + (uint64_t)q * kThreads;
+            if (u >= n_units) continue;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const R p = A[q][e].x * A[q][e].x + A[q][e].y * A[q][e].y;
+                if (__popcll((u * V + e) & mask) & 1) run[1] += p; else run[0] += p;
+            }
+        }
+        if (++iter == kRun) {
+            tot[0] += (double)run[0];
+            tot[1] += (double)run[1];
+            run[0] = run[1] = R(0);
+            iter = 0;
+        }
+    }
+    tot[0] += (double)run[0];
+    tot[1] += (double)run[1];
+    block_reduce_store<2>(tot, 2, partials + (size_t)blockIdx.x * 8);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_collapse(typename CT<R>::T *__restrict__ sv, uint64_t n_units, uint64_t mask, int parity, R scale) {
+    using C = typename CT<R>::T;
+    constexpr int V = CT<R>::V;
+    const uint64_t u = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (u >= n_units) return;
+    C A[V];
+    load_unit<R>(sv, u, A);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const bool keep = (int)(__popcll((u * V + e) & mask) & 1) == parity;
+        A[e].x = keep ? A[e].x * scale : R(0);
+        A[e].y = keep ? A[e].y * scale : R(0);
+    }
+    if constexpr (V == 2) {
+        reinterpret_cast<float4 *>(sv)[u] = make_float4(A[0].x, A[0].y, A[1].x, A[1].y);
+    } else {
+        sv[u] = A[0];
+    }
+}
+
+template <typename R>
+__global__ void k_set_one(typename CT<R>::T *sv, uint64_t index) {
+    sv[index] = typename CT<R>::T{R(1), R(0)};
+}
+
+inline int reduce_grid(const LaunchCtx &L, uint64_t work, int max_blocks) {
+    uint64_t b = (work + (uint64_t)kThreads * kIlp - 1) / ((uint64_t)kThreads * kIlp);
+    uint64_t cap = (uint64_t)L.num_sms * 8;
+    if (cap > (uint64_t)max_blocks) cap = (uint64_t)max_blocks;
+    if (b > cap) b = cap;
+    return (int)(b == 0 ? 1 : b);
+}
+
+template <typename R>
+cudaError_t pauli_t(const LaunchCtx &L, const void *sv, int n, const PauliPass &P, double *d_partials, int maxb,
+                    double *d_out) {
+    using C = typename CT<R>::T;
+    constexpr int V = CT<R>::V;
+    const int vb = V == 2 ? 1 : 0;                   // log2 V
+    const uint64_t n_units = (1ull << n) >> vb;
+    const unsigned xl = (unsigned)(P.x & (V - 1));
+    const uint64_t xu = P.x >> vb;
+    int pair_bit = -1;
+    uint64_t n_work = n_units;
+    if (xu != 0) {
+        pair_bit = __builtin_ctzll(xu);
+        n_work = n_units / 2;
+    }
+    const int grid = reduce_grid(L, n_work, maxb);
+    k_pauli<R><<<grid, kThreads, 0, L.stream>>>(reinterpret_cast<const C *>(sv), n_work, pair_bit, xu, xl, P,
+                                                d_partials);
+    ++*L.launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_finish<<<1, kThreads, 0, L.stream>>>(d_partials, grid, P.S, P, 1, d_out);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t parity_t(const LaunchCtx &L, const void *sv, int n, uint64_t mask, double *d_partials, int maxb,
+                     double *d_out) {
+    using C = typename CT<R>::T;
+    constexpr int V = CT<R>::V;
+    const uint64_t n_units = (1ull << n) / V;
+    const int grid = reduce_grid(L, n_units, maxb);
+    k_parity<R><<<grid, kThreads, 0, L.stream>>>(reinterpret_cast<const C *>(sv), n_units, mask, d_partials);
+    ++*L.launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    PauliPass none{};
+    k_finish<<<1, kThreads, 0, L.stream>>>(d_partials, grid, 2, none, 0, d_out);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t collapse_t(const LaunchCtx &L, void *sv, int n, uint64_t mask, int parity, double scale) {
+    using C = typename CT<R>::T;
+    constexpr int V = CT<R>::V;
+    const uint64_t n_units = (1ull << n) / V;
+    const uint64_t grid = (n_units + kThreads - 1) / kThreads;
+    k_collapse<R><<<(unsigned)grid, kThreads, 0, L.stream>>>(reinterpret_cast<C *>(sv), n_units, mask, parity,
+                                                             (R)scale);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_pauli(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int n, const PauliPass &P,
+                         double *d_partials, int max_partial_blocks, double *d_out) {
+    if (n < 1) return cudaErrorInvalidValue;
+    return dt == SV_C64 ? pauli_t<float>(L, sv, n, P, d_partials, max_partial_blocks, d_out)
+                        : pauli_t<double>(L, sv, n, P, d_partials, max_partial_blocks, d_out);
+}
+
+cudaError_t launch_parity(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int n, uint64_t mask,
+                          double *d_partials, int max_partial_blocks, double *d_out) {
+    if (n < 1) return cudaErrorInvalidValue;
+    return dt == SV_C64 ? parity_t<float>(L, sv, n, mask, d_partials, max_partial_blocks, d_out)
+                        : parity_t<double>(L, sv, n, mask, d_partials, max_partial_blocks, d_out);
+}
+
+cudaError_t launch_collapse(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t mask, int parity,
+                            double scale) {
+    if (n < 1) return cudaErrorInvalidValue;
+    return dt == SV_C64 ? collapse_t<float>(L, sv, n, mask, parity, scale)
+                        : collapse_t<double>(L, sv, n, mask, parity, scale);
+}
+
+cudaError_t launch_set_basis(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t index) {
+    const size_t bytes = (size_t(1) << n) * (dt == SV_C64 ? 8 : 16);
+    cudaError_t e = cudaMemsetAsync(sv, 0, bytes, L.stream);
+    if (e != cudaSuccess) return e;
+    if (dt == SV_C64)
+        k_set_one<float><<<1, 1, 0, L.stream>>>(reinterpret_cast<float2 *>(sv), index);
+    else
+        k_set_one<double><<<1, 1, 0, L.stream>>>(reinterpret_cast<double2 *>(sv), index);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+}  // namespace svk

@@ -1,0 +1,150 @@
+// sv_fuse.cpp -- host gate fusion (Sec. II-B: fusing many small gate matrices
+// into one multi-qubit matrix applied in one pass; the width limit is qsim's
+// max_fused_gate_size, Sec. II-D-1).
+//
+// The paper gives the idea and the width option, not an algorithm; the one here
+// is a greedy pass in program order that may move a gate earlier only past
+// blocks that share no qubit with it (such gates commute, so the product is
+// unchanged). Block matrices are composed in FP64 by applying each absorbed
+// gate to every column of the block matrix.
+#include "sv_fuse.h"
+
+#include <algorithm>
+#include <cstdint>
+
+namespace svf {
+
+void apply_small(cd *psi, int s, const int *targets, int k, const int *controls, const int *cvals, int c,
+                 const cd *m) {
+    const uint64_t N = 1ull << s, D = 1ull << k;
+    uint64_t tmask = 0, cmask = 0, cwant = 0;
+    for (int t = 0; t < k; ++t) tmask |= 1ull << targets[t];
+    for (int t = 0; t < c; ++t) {
+        cmask |= 1ull << controls[t];
+        if (cvals[t]) cwant |= 1ull << controls[t];
+    }
+    uint64_t off[64];
+    for (uint64_t j = 0; j < D; ++j) {
+        uint64_t o = 0;
+        for (int t = 0; t < k; ++t)
+            if ((j >> t) & 1) o |= 1ull << targets[t];
+        off[j] = o;
+    }
+    cd in[64];
+    for (uint64_t b = 0; b < N; ++b) {
+        if ((b & tmask) || (b & cmask) != cwant) continue;
+        for (uint64_t l = 0; l < D; ++l) in[l] = psi[b | off[l]];
+        for (uint64_t j = 0; j < D; ++j) {
+            cd acc = 0;
+            for (uint64_t l = 0; l < D; ++l) acc += m[j * D + l] * in[l];
+            psi[b | off[j]] = acc;
+        }
+    }
+}
+
+namespace {
+
+int local_index(const std::vector<int> &qs, int q) {
+    for (size_t i = 0; i < qs.size(); ++i)
+        if (qs[i] == q) return (int)i;
+    return -1;
+}
+
+// Grow the block to include `extra` qubits (appended as higher index bits):
+// B <- I (x) B.
+void grow(Item &b, const std::vector<int> &extra) {
+    if (extra.empty()) return;
+    const int s = (int)b.qubits.size();
+    const int s2 = s + (int)extra.size();
+    const uint64_t d = 1ull << s, d2 = 1ull << s2;
+    std::vector<cd> m2(d2 * d2, cd(0));
+    for (uint64_t r = 0; r < d2; ++r)
+        for (uint64_t c = 0; c < d2; ++c)
+            if ((r >> s) == (c >> s)) m2[r * d2 + c] = b.m[(r & (d - 1)) * d + (c & (d - 1))];
+    b.m.swap(m2);
+    b.qubits.insert(b.qubits.end(), extra.begin(), extra.end());
+}
+
+// B <- G B, G the gate embedded in the block's basis
+void absorb(Item &b, const sv_gate_t &g) {
+    std::vector<int> extra;
+    for (int t = 0; t < g.n_targets + g.n_controls; ++t) {
+        const int q = t < g.n_targets ? g.targets[t] : g.controls[t - g.n_targets];
+        if (local_index(b.qubits, q) < 0) extra.push_back(q);
+    }
+    grow(b, extra);
+    const int s = (int)b.qubits.size();
+    int lt[SV_MAX_TARGETS], lc[SV_MAX_CONTROLS], cv[SV_MAX_CONTROLS];
+    for (int t = 0; t < g.n_targets; ++t) lt[t] = local_index(b.qubits, g.targets[t]);
+    for (int t = 0; t < g.n_controls; ++t) {
+        lc[t] = local_index(b.qubits, g.controls[t]);
+        cv[t] = g.control_values[t] ? 1 : 0;
+    }
+    const uint64_t d = 1ull << s, D = 1ull << g.n_targets;
+    std::vector<cd> gm(D * D);
+    for (uint64_t i = 0; i < D * D; ++i) gm[i] = cd(g.matrix[2 * i], g.matrix[2 * i + 1]);
+    // apply to each column of B (column c = B[:, c])
+    std::vector<cd> col(d);
+    for (uint64_t c = 0; c < d; ++c) {
+        for (uint64_t r = 0; r < d; ++r) col[r] = b.m[r * d + c];
+        apply_small(col.data(), s, lt, g.n_targets, lc, cv, g.n_controls, gm.data());
+        for (uint64_t r = 0; r < d; ++r) b.m[r * d + c] = col[r];
+    }
+    ++b.n_gates;
+}
+
+}  // namespace
+
+sv_status_t fuse(const sv_gate_t *gates, int n_gates, int n_qubits, int width, std::vector<Item> &out) {
+    out.clear();
+    if (width < 1 || width > SV_MAX_TARGETS || n_qubits < 1 || n_qubits > SV_MAX_QUBITS || n_gates < 0)
+        return SV_ERR_INVALID_ARGUMENT;
+    std::vector<int> last(n_qubits, -1);   // latest item touching each qubit
+    constexpr int kScan = 64;              // blocks examined per gate
+    for (int gi = 0; gi < n_gates; ++gi) {
+        const sv_gate_t &g = gates[gi];
+        const int nq = g.n_targets + g.n_controls;
+        int L = -1;
+        std::vector<int> Q(nq);
+        for (int t = 0; t < nq; ++t) {
+            Q[t] = t < g.n_targets ? g.targets[t] : g.controls[t - g.n_targets];
+            L = std::max(L, last[Q[t]]);
+        }
+        if (nq > width) {
+            Item it;
+            it.passthrough = true;
+            it.gate = gi;
+            it.n_gates = 1;
+            out.push_back(std::move(it));
+            for (int q : Q) last[q] = (int)out.size() - 1;
+            continue;
+        }
+        int best = -1, best_growth = 1 << 30;
+        const int lo = std::max({L, 0, (int)out.size() - kScan});
+        for (int j = (int)out.size() - 1; j >= lo; --j) {
+            const Item &b = out[j];
+            if (b.passthrough) continue;
+            int growth = 0;
+            for (int q : Q)
+                if (local_index(b.qubits, q) < 0) ++growth;
+            if ((int)b.qubits.size() + growth <= width && growth < best_growth) {
+                best = j;
+                best_growth = growth;
+            }
+        }
+        if (best < 0) {
+            Item it;
+            it.qubits = Q;
+            const uint64_t d = 1ull << nq;
+            it.m.assign(d * d, cd(0));
+            for (uint64_t i = 0; i < d; ++i) it.m[i * d + i] = 1;
+            out.push_back(std::move(it));
+            best = (int)out.size() - 1;
+        }
+        absorb(out[best], g);
+        for (int q : Q) last[q] = best;
+    }
+    return SV_OK;
+}
+
+}  // namespace svf

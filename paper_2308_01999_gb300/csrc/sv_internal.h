@@ -1,0 +1,78 @@
+// sv_internal.h -- types shared by the host API and the kernels of libsv.so.
+//
+// Index geometry. For a gate with k targets and c controls on an n-qubit
+// state, the 2^(n-k-c) amplitude groups are numbered g = 0, 1, ...; the first
+// amplitude of group g is g with a zero bit inserted at every target and
+// control position (in ascending order), with the control bits then set to
+// their required values (Sec. II-C: each index bit is one qubit). Member j of
+// the group adds bit t of j at target position t.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sv.h"
+
+namespace svk {
+
+constexpr int kMaxSpecial = SV_MAX_TARGETS + SV_MAX_CONTROLS;
+
+// Sorted positions at which zero bits are inserted, plus the bits forced to 1.
+struct GroupGeom {
+    int ns;                 // number of inserted positions
+    int pos[kMaxSpecial];   // ascending
+    uint64_t cset;          // control bits whose required value is 1
+};
+
+// 1 << targets[t], targets ascending.
+struct TargetOffs {
+    uint64_t t[SV_MAX_TARGETS];
+};
+
+// Launch bookkeeping shared by every launch wrapper.
+struct LaunchCtx {
+    cudaStream_t stream;
+    int num_sms;
+    uint64_t *launches;     // incremented once per kernel launch
+};
+
+// ---- gate kernels (k_gate.cu) ----
+// Dense 2^k x 2^k product on every group, k = 1..6. `mat` is row-major
+// complex128 for targets in ascending order. `d_mat` is workspace for k >= 5.
+cudaError_t launch_dense(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, const GroupGeom &G,
+                         const int *tpos, int k, const double *mat, void *d_mat);
+// Diagonal d[j] on targets (any order; j's bit t is targets[t]) where controls hold, k = 0..6.
+cudaError_t launch_diag(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, const GroupGeom &Gctl,
+                        const int *tpos, int k, const double *diag);
+// Generalized permutation: out[j] = d[j] * in[perm[j]] per group, k = 1..4, targets ascending.
+cudaError_t launch_perm(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, const GroupGeom &G,
+                        const int *tpos, int k, const int *perm, const double *d);
+
+// ---- reductions (k_reduce.cu) ----
+struct PauliPass {
+    int S;              // strings in this pass (1..8)
+    uint64_t x;         // common X|Y mask
+    uint64_t z[8];      // Z|Y mask per string
+    int use_im[8];      // take Im(w) instead of Re(w) (odd number of Y)
+    double sign[8];     // +1 / -1 from i^{nY}
+};
+constexpr int kPauliMaxS = 8;
+// Writes S doubles at d_out (device).
+cudaError_t launch_pauli(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int n, const PauliPass &P,
+                         double *d_partials, int max_partial_blocks, double *d_out);
+// d_out[0] = sum over even parity of mask, d_out[1] = odd.
+cudaError_t launch_parity(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int n, uint64_t mask,
+                          double *d_partials, int max_partial_blocks, double *d_out);
+cudaError_t launch_collapse(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t mask,
+                            int parity, double scale);
+cudaError_t launch_set_basis(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t index);
+
+// ---- tensor-core fused apply (k_tc.cu) ----
+// psi <- G psi for a 6-target block with G given as 64x64 complex128,
+// targets ascending; prec = SV_PREC_TF32 or SV_PREC_SPLIT_BF16; c64 only.
+// d_a: workspace for the staged operand (>= 64 KiB); d_err: device status word.
+cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, const double *mat,
+                       sv_precision_t prec, void *d_a, int *d_err);
+bool tc6_supported(int n, const int *tpos);
+
+}  // namespace svk

@@ -1,0 +1,339 @@
+"""Python binding of libsv.so: the same calls as ``include/sv.h``, argument
+marshalling only.
+
+Device memory and streams come from PyTorch: a state is a CUDA tensor of
+dtype complex64 or complex128 with 2^n elements, owned by the caller (the
+library borrows its pointer, as the paper's relaxed memory model has it,
+Sec. II-A). Every step of the computation runs in the CUDA library; there is
+no CPU or PyTorch fallback, and loading fails loudly when ``libsv.so`` is
+missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "SvError", "lib", "sv_create", "sv_destroy", "sv_set_stream", "sv_set_state_pointer",
+    "sv_set_basis_state", "sv_copy_from_host", "sv_copy_to_host", "sv_apply_matrix",
+    "sv_apply_fused", "sv_fuse_plan", "sv_expectation_pauli", "sv_measure_probs", "sv_collapse",
+    "sv_measure", "sv_norm2", "sv_check_device_status", "sv_launch_count", "sv_status_string",
+    "SV_C64", "SV_C128", "SV_PREC_NATIVE", "SV_PREC_TF32", "SV_PREC_SPLIT_BF16", "StateVector",
+    "EXPORTED",
+]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsv.so")
+
+SV_C64, SV_C128 = 0, 1
+SV_PREC_NATIVE, SV_PREC_TF32, SV_PREC_SPLIT_BF16 = 0, 1, 2
+SV_MAX_TARGETS, SV_MAX_CONTROLS = 6, 24
+STATUS = {0: "SV_OK", 1: "SV_ERR_INVALID_ARGUMENT", 2: "SV_ERR_NOT_SUPPORTED",
+          3: "SV_ERR_INSUFFICIENT_WORKSPACE", 4: "SV_ERR_CUDA", 5: "SV_ERR_TIMEOUT", 6: "SV_ERR_ALLOC"}
+
+# every entry point declared in include/sv.h
+EXPORTED = [
+    "sv_create", "sv_destroy", "sv_set_stream", "sv_set_state_pointer", "sv_set_basis_state",
+    "sv_copy_from_host", "sv_copy_to_host", "sv_apply_matrix", "sv_apply_fused", "sv_fuse_plan",
+    "sv_expectation_pauli", "sv_measure_probs", "sv_collapse", "sv_measure", "sv_norm2",
+    "sv_check_device_status", "sv_launch_count", "sv_status_string",
+]
+
+
+class SvError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class sv_gate_t(C.Structure):
+    _fields_ = [("n_targets", C.c_int), ("targets", C.c_int * SV_MAX_TARGETS),
+                ("n_controls", C.c_int), ("controls", C.c_int * SV_MAX_CONTROLS),
+                ("control_values", C.c_int * SV_MAX_CONTROLS), ("matrix", C.POINTER(C.c_double))]
+
+
+_lib = None
+_VP, _I, _D = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
+
+
+def lib():
+    """Load libsv.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2308_01999_gb300._build` (no fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        sig = {
+            "sv_create": [C.c_int, C.c_int, _VP, _VP, C.POINTER(_VP)],
+            "sv_destroy": [_VP], "sv_set_stream": [_VP, _VP], "sv_set_state_pointer": [_VP, _VP],
+            "sv_set_basis_state": [_VP, C.c_uint64],
+            "sv_copy_from_host": [_VP, _VP], "sv_copy_to_host": [_VP, _VP],
+            "sv_apply_matrix": [_VP, _I, C.c_int, _I, _I, C.c_int, _D, C.c_int],
+            "sv_apply_fused": [_VP, C.POINTER(sv_gate_t), C.c_int, C.c_int, C.c_int, _I],
+            "sv_fuse_plan": [C.POINTER(sv_gate_t), C.c_int, C.c_int, C.c_int, C.c_int, _I, _I, _I, _D],
+            "sv_expectation_pauli": [_VP, _I, _I, C.c_int, C.c_int, _D],
+            "sv_measure_probs": [_VP, _I, C.c_int, _D, _D],
+            "sv_collapse": [_VP, _I, C.c_int, C.c_int, C.c_double],
+            "sv_measure": [_VP, _I, C.c_int, C.c_double, C.c_int, _I],
+            "sv_norm2": [_VP, _D], "sv_check_device_status": [_VP],
+            "sv_launch_count": [_VP, C.POINTER(C.c_uint64)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.sv_status_string.argtypes = [C.c_int]
+        L.sv_status_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise SvError(code, where)
+
+
+def _ints(xs):
+    a = np.ascontiguousarray(np.asarray(list(xs) if not isinstance(xs, np.ndarray) else xs,
+                                        dtype=np.int32).reshape(-1))
+    return a, (a.ctypes.data_as(_I) if a.size else None)
+
+
+def _cmat(m):
+    a = np.ascontiguousarray(np.asarray(m, dtype=np.complex128))
+    return a, a.ctypes.data_as(_D)
+
+
+# ---- thin wrappers with the ABI's names ----
+
+def sv_status_string(code: int) -> str:
+    return lib().sv_status_string(int(code)).decode()
+
+
+def sv_create(n_qubits: int, dtype: int, d_state_ptr: int, stream_ptr: int = 0) -> int:
+    h = _VP()
+    _check(lib().sv_create(int(n_qubits), int(dtype), _VP(d_state_ptr), _VP(stream_ptr), C.byref(h)), "sv_create")
+    return h.value
+
+
+def sv_destroy(h: int):
+    _check(lib().sv_destroy(_VP(h)), "sv_destroy")
+
+
+def sv_set_stream(h: int, stream_ptr: int):
+    _check(lib().sv_set_stream(_VP(h), _VP(stream_ptr)), "sv_set_stream")
+
+
+def sv_set_state_pointer(h: int, d_state_ptr: int):
+    _check(lib().sv_set_state_pointer(_VP(h), _VP(d_state_ptr)), "sv_set_state_pointer")
+
+
+def sv_set_basis_state(h: int, index: int):
+    _check(lib().sv_set_basis_state(_VP(h), C.c_uint64(index)), "sv_set_basis_state")
+
+
+def sv_copy_from_host(h: int, host_ptr: int):
+    _check(lib().sv_copy_from_host(_VP(h), _VP(host_ptr)), "sv_copy_from_host")
+
+
+def sv_copy_to_host(h: int, host_ptr: int):
+    _check(lib().sv_copy_to_host(_VP(h), _VP(host_ptr)), "sv_copy_to_host")
+
+
+def sv_apply_matrix(h: int, targets, matrix, controls=(), control_values=None, adjoint: bool = False):
+    t, tp = _ints(targets)
+    c, cp = _ints(controls)
+    if control_values is not None and len(control_values):
+        cv, cvp = _ints(control_values)
+    else:
+        cv, cvp = None, None
+    m, mp = _cmat(matrix)
+    if m.shape != (1 << t.size, 1 << t.size):
+        raise ValueError("matrix shape does not match the number of targets")
+    _check(lib().sv_apply_matrix(_VP(h), tp, int(t.size), cp, cvp, int(c.size), mp, int(bool(adjoint))),
+           "sv_apply_matrix")
+
+
+def _gate_array(gates):
+    arr = (sv_gate_t * max(1, len(gates)))()
+    keep = []
+    for i, g in enumerate(gates):
+        m, mp = _cmat(g.matrix)
+        keep.append(m)
+        s = arr[i]
+        s.n_targets = len(g.targets)
+        for j, q in enumerate(g.targets):
+            s.targets[j] = int(q)
+        s.n_controls = len(g.controls)
+        cv = tuple(g.control_values) if g.control_values else (1,) * len(g.controls)
+        for j, q in enumerate(g.controls):
+            s.controls[j] = int(q)
+            s.control_values[j] = int(cv[j])
+        s.matrix = mp
+    return arr, keep
+
+
+def sv_apply_fused(h: int, gates, max_fused_qubits: int, prec: int = SV_PREC_NATIVE) -> int:
+    """Apply ``gates`` (objects with targets/matrix/controls/control_values) fused; returns the block count."""
+    arr, _keep = _gate_array(gates)
+    nf = C.c_int(0)
+    _check(lib().sv_apply_fused(_VP(h), arr, len(gates), int(max_fused_qubits), int(prec), C.byref(nf)),
+           "sv_apply_fused")
+    return nf.value
+
+
+def sv_fuse_plan(gates, n_qubits: int, max_fused_qubits: int, max_blocks: int | None = None):
+    """Host-only fusion plan: list of (targets tuple, matrix) in application order."""
+    arr, _keep = _gate_array(gates)
+    cap = max_blocks if max_blocks is not None else max(1, len(gates))
+    nb = C.c_int(0)
+    ks = np.zeros(cap, dtype=np.int32)
+    ts = np.zeros(cap * SV_MAX_TARGETS, dtype=np.int32)
+    ms = np.zeros(cap * 64 * 64 * 2, dtype=np.float64)
+    _check(lib().sv_fuse_plan(arr, len(gates), int(n_qubits), int(max_fused_qubits), cap, C.byref(nb),
+                              ks.ctypes.data_as(_I), ts.ctypes.data_as(_I), ms.ctypes.data_as(_D)),
+           "sv_fuse_plan")
+    out = []
+    for b in range(nb.value):
+        k = int(ks[b])
+        d = 1 << k
+        flat = ms[b * 8192: b * 8192 + 2 * d * d]
+        out.append((tuple(int(x) for x in ts[b * SV_MAX_TARGETS: b * SV_MAX_TARGETS + k]),
+                    (flat[0::2] + 1j * flat[1::2]).reshape(d, d)))
+    return out
+
+
+def sv_expectation_pauli(h: int, paulis, sites) -> np.ndarray:
+    """paulis, sites: int arrays of shape (n_strings, n_sites). Returns float64 (n_strings,)."""
+    p = np.ascontiguousarray(np.asarray(paulis, dtype=np.int32))
+    s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
+    if p.ndim == 1:
+        p, s = p[None, :], s[None, :]
+    if p.shape != s.shape:
+        raise ValueError("paulis and sites must have the same shape")
+    out = np.zeros(p.shape[0], dtype=np.float64)
+    _check(lib().sv_expectation_pauli(_VP(h), p.ctypes.data_as(_I), s.ctypes.data_as(_I), int(p.shape[1]),
+                                      int(p.shape[0]), out.ctypes.data_as(_D)), "sv_expectation_pauli")
+    return out
+
+
+def sv_measure_probs(h: int, qubits):
+    q, qp = _ints(qubits)
+    a, b = C.c_double(), C.c_double()
+    _check(lib().sv_measure_probs(_VP(h), qp, int(q.size), C.byref(a), C.byref(b)), "sv_measure_probs")
+    return a.value, b.value
+
+
+def sv_collapse(h: int, qubits, parity: int, prob: float):
+    q, qp = _ints(qubits)
+    _check(lib().sv_collapse(_VP(h), qp, int(q.size), int(parity), float(prob)), "sv_collapse")
+
+
+def sv_measure(h: int, qubits, randnum: float, collapse: bool) -> int:
+    q, qp = _ints(qubits)
+    out = C.c_int(-1)
+    _check(lib().sv_measure(_VP(h), qp, int(q.size), float(randnum), int(bool(collapse)), C.byref(out)),
+           "sv_measure")
+    return out.value
+
+
+def sv_norm2(h: int) -> float:
+    v = C.c_double()
+    _check(lib().sv_norm2(_VP(h), C.byref(v)), "sv_norm2")
+    return v.value
+
+
+def sv_check_device_status(h: int) -> int:
+    return int(lib().sv_check_device_status(_VP(h)))
+
+
+def sv_launch_count(h: int) -> int:
+    v = C.c_uint64()
+    _check(lib().sv_launch_count(_VP(h), C.byref(v)), "sv_launch_count")
+    return int(v.value)
+
+
+# ---- convenience: a handle bound to a torch tensor ----
+
+@dataclass
+class StateVector:
+    """A handle over a caller-owned CUDA tensor (complex64 / complex128, 2^n elements)."""
+
+    state: object          # torch.Tensor
+    stream: object = None  # torch.cuda.Stream (None = current stream)
+
+    def __post_init__(self):
+        import torch
+        t = self.state
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("state must be a contiguous CUDA tensor")
+        if t.dtype == torch.complex64:
+            self.dtype = SV_C64
+        elif t.dtype == torch.complex128:
+            self.dtype = SV_C128
+        else:
+            raise ValueError("state dtype must be complex64 or complex128")
+        self.n = int(t.numel()).bit_length() - 1
+        if (1 << self.n) != t.numel():
+            raise ValueError("state length must be a power of two")
+        if self.stream is None:
+            self.stream = torch.cuda.current_stream(t.device)
+        with torch.cuda.device(t.device):
+            self.handle = sv_create(self.n, self.dtype, t.data_ptr(), self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_basis_state(self, index: int = 0):
+        sv_set_basis_state(self.handle, index)
+
+    def apply(self, targets, matrix, controls=(), control_values=None, adjoint=False):
+        sv_apply_matrix(self.handle, targets, matrix, controls, control_values, adjoint)
+
+    def apply_gate(self, g, adjoint=False):
+        sv_apply_matrix(self.handle, g.targets, g.matrix, g.controls, g.control_values or None, adjoint)
+
+    def apply_circuit(self, gates):
+        for g in gates:
+            self.apply_gate(g)
+
+    def apply_fused(self, gates, max_fused_qubits: int, prec: int = SV_PREC_NATIVE) -> int:
+        return sv_apply_fused(self.handle, gates, max_fused_qubits, prec)
+
+    def expectation_pauli(self, paulis, sites):
+        return sv_expectation_pauli(self.handle, paulis, sites)
+
+    def expectation_z_all(self):
+        n = self.n
+        return sv_expectation_pauli(self.handle, np.full((n, 1), 3, np.int32), np.arange(n, dtype=np.int32)[:, None])
+
+    def measure_probs(self, qubits):
+        return sv_measure_probs(self.handle, qubits)
+
+    def collapse(self, qubits, parity, prob):
+        sv_collapse(self.handle, qubits, parity, prob)
+
+    def measure(self, qubits, randnum, collapse=False):
+        return sv_measure(self.handle, qubits, randnum, collapse)
+
+    def norm2(self):
+        return sv_norm2(self.handle)
+
+    def check(self):
+        code = sv_check_device_status(self.handle)
+        if code != 0:
+            raise SvError(code, "device status")
+
+    def launches(self) -> int:
+        return sv_launch_count(self.handle)

@@ -1,0 +1,87 @@
+"""CPU-only checks of libsv.so: it loads, exports every entry point that
+include/sv.h declares, and its host-side fusion pass (Sec. II-B) composes
+blocks that reproduce the unfused circuit under the oracle. No GPU call."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2308_01999_gb300 import inputs as gen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sv():
+    from paper_2308_01999_gb300 import _build
+    _build.build()
+    from paper_2308_01999_gb300 import sv as mod
+    mod.lib()
+    return mod
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "sv.h")).read()
+    return sorted(set(re.findall(r"^SV_API\s+[^()]*?\b(sv_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_library_exports_every_declared_entry_point(sv):
+    declared = header_functions()
+    assert len(declared) >= 18
+    L = sv.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert sorted(sv.EXPORTED) == declared
+
+
+def test_status_strings(sv):
+    assert sv.sv_status_string(0) == "SV_OK"
+    assert sv.sv_status_string(1) == "SV_ERR_INVALID_ARGUMENT"
+    assert sv.sv_status_string(5) == "SV_ERR_TIMEOUT"
+    assert sv.sv_status_string(99) == "SV_ERR_UNKNOWN"
+
+
+def _apply_plan(plan, n):
+    psi = orc.zero_state(n)
+    for targets, m in plan:
+        orc.apply_gate(psi, list(targets), m)
+    return psi
+
+
+@pytest.mark.parametrize("width", [1, 2, 3, 4, 5, 6])
+def test_fusion_plan_reproduces_unfused_circuit(sv, width):
+    n = 9
+    gates = gen.layered_random_circuit(n, 6, seed=40 + width, kinds=("cz", "cnot", "crz"))
+    ref = orc.run_circuit(gates, n)
+    plan = sv.sv_fuse_plan(gates, n, width)
+    assert all(len(t) <= max(width, 2) for t, _ in plan)
+    if width >= 4:
+        assert len(plan) < len(gates) / 3
+    got = _apply_plan(plan, n)
+    np.testing.assert_allclose(got, ref, atol=1e-12, rtol=0)
+
+
+def test_fusion_of_brick_wall_and_controls(sv):
+    n = 10
+    gates = gen.circuit_config2(n=n, layers=8, seed=5)
+    rng = gen.rng_for(6)
+    # add multi-qubit and multi-control gates, incl. control value 0
+    for _ in range(10):
+        qs = [int(x) for x in rng.choice(n, 4, replace=False)]
+        gates.append(gen.Gate((qs[0], qs[1]), gen.random_gate_dense(rng, 2), (qs[2], qs[3]), (0, 1)))
+    ref = orc.run_circuit(gates, n)
+    for w in (3, 5, 6):
+        plan = sv.sv_fuse_plan(gates, n, w)
+        np.testing.assert_allclose(_apply_plan(plan, n), ref, atol=1e-12, rtol=0)
+
+
+def test_fusion_rejects_bad_gates(sv):
+    bad = [gen.Gate((0, 0), np.eye(4))]
+    with pytest.raises(sv.SvError):
+        sv.sv_fuse_plan(bad, 3, 2)
+    with pytest.raises(sv.SvError):
+        sv.sv_fuse_plan([gen.Gate((3,), np.eye(2))], 3, 2)
+    with pytest.raises(sv.SvError):
+        sv.sv_fuse_plan([gen.Gate((0,), np.eye(2))], 3, 7)

@@ -1,0 +1,318 @@
+"""GPU parity: libsv.so (through its C ABI) against the CPU oracle, element by
+element on the same seeded inputs.
+
+Tolerances (stated by the build's target): max |d amplitude| <= 1e-12 for
+complex128 and <= 1e-5 for complex64; expectation values and probabilities
+within 1e-6 * max(1, |ref|) for complex64 and 1e-12 for complex128.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2308_01999_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+AMP_TOL = {"c128": 1e-12, "c64": 1e-5}
+EXP_TOL = {"c128": 1e-12, "c64": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2308_01999_gb300 import sv
+    sv.lib()
+    return torch, sv
+
+
+def tdtype(torch, name):
+    return torch.complex128 if name == "c128" else torch.complex64
+
+
+def make_state(env, n, name, init=None):
+    torch, sv = env
+    if init is None:
+        psi = torch.zeros(1 << n, dtype=tdtype(torch, name), device="cuda")
+        s = sv.StateVector(psi)
+        s.set_basis_state(0)
+    else:
+        psi = torch.from_numpy(init.astype(np.complex128)).to(tdtype(torch, name)).cuda()
+        s = sv.StateVector(psi)
+    return psi, s
+
+
+def host(psi):
+    return psi.cpu().numpy().astype(np.complex128)
+
+
+def assert_amps(got, ref, name, what=""):
+    err = np.max(np.abs(got - ref)) if ref.size else 0.0
+    assert err <= AMP_TOL[name], f"{what} max|d amp| = {err:.3e} > {AMP_TOL[name]}"
+
+
+def assert_exp(got, ref, name, what=""):
+    got, ref = np.asarray(got, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    bound = EXP_TOL[name] * np.maximum(1.0, np.abs(ref))
+    bad = np.abs(got - ref) > bound
+    assert not bad.any(), f"{what} expectation mismatch: {got[bad]} vs {ref[bad]}"
+
+
+NAMES = ["c128", "c64"]
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_config0_circuit_amplitudes_and_z(env, name):
+    n = 16
+    gates = gen.circuit_config0(0)
+    ref = orc.run_circuit(gates, n)
+    psi, s = make_state(env, n, name)
+    s.apply_circuit(gates)
+    assert_amps(host(psi), ref, name, "config0")
+    z = s.expectation_z_all()
+    assert_exp(z, orc.expect_z_all(ref), name, "<Z_q>")
+    assert abs(s.norm2() - 1) <= EXP_TOL[name]
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_one_qubit_gate_on_every_position(env, name):
+    n = 13
+    rng = gen.rng_for(21)
+    init = gen.random_state(n, 21)
+    ref = init.copy()
+    psi, s = make_state(env, n, name, init)
+    for q in range(n):
+        u = gen.haar_su2(rng)
+        s.apply([q], u)
+        orc.apply_gate(ref, [q], u)
+    assert_amps(host(psi), ref, name, "1q sweep")
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_dense_gates_random_targets_and_controls(env, name, k):
+    n = 11
+    rng = gen.rng_for(100 + k)
+    init = gen.random_state(n, 100 + k)
+    ref = init.copy()
+    psi, s = make_state(env, n, name, init)
+    for it in range(8):
+        c = int(rng.integers(0, min(3, n - k) + 1))
+        qs = [int(x) for x in rng.choice(n, k + c, replace=False)]
+        if it == 0:
+            qs = list(range(k + c))            # lowest bits: target (or control) on bit 0
+        elif it == 1:
+            qs = list(range(n - k - c, n))     # highest bits
+        t, ctl = qs[:k], qs[k:]
+        cv = [int(v) for v in rng.integers(0, 2, size=c)]
+        m = gen.random_gate_dense(rng, k)
+        adj = bool(it % 3 == 2)
+        s.apply(t, m, ctl, cv, adjoint=adj)
+        orc.apply_gate(ref, t, m.conj().T if adj else m, ctl, cv)
+    assert_amps(host(psi), ref, name, f"k={k}")
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_structured_gates(env, name):
+    """Diagonal, generalized-permutation and control-revealing dense matrices
+    (exercises the structure analysis), incl. bit-0 controls and targets."""
+    n = 10
+    rng = gen.rng_for(7)
+    init = gen.random_state(n, 7)
+    ref = init.copy()
+    psi, s = make_state(env, n, name, init)
+    ops = []
+    for a, b in [(0, 1), (1, 0), (5, 9), (9, 2), (3, 0)]:
+        ops.append(gen.dense_form(gen.cz(a, b)))
+        ops.append(gen.dense_form(gen.cnot(a, b)))
+        ops.append(gen.dense_form(gen.crz(a, b, float(rng.uniform(0, 6.28)))))
+        ops.append(gen.cz(a, b))
+        ops.append(gen.cnot(a, b))
+        ops.append(gen.crz(a, b, 1.1))
+    for k in range(1, 7):
+        qs = [int(x) for x in rng.choice(n, k + 1, replace=False)]
+        d = np.exp(1j * rng.uniform(0, 6.28, size=1 << k))
+        ops.append(gen.Gate(tuple(qs[:k]), np.diag(d), (qs[k],), (int(rng.integers(0, 2)),)))
+        ops.append(gen.Gate(tuple(qs[:k]), np.diag(d)))
+        perm = rng.permutation(1 << k)
+        pm = np.zeros((1 << k, 1 << k), dtype=np.complex128)
+        pm[np.arange(1 << k), perm] = np.exp(1j * rng.uniform(0, 6.28, size=1 << k))
+        ops.append(gen.Gate(tuple(qs[:k]), pm, (qs[k],), (1,)))
+        ops.append(gen.Gate(tuple(qs[:k]), pm))
+    ops.append(gen.Gate((4,), gen.gate_phase(0.3)))
+    ops.append(gen.Gate((0,), gen.gate_phase(-0.7), (1, 2), (1, 0)))
+    ops.append(gen.Gate((2, 7), np.eye(4)))
+    ops.append(gen.Gate((0, 5), gen.gate_swap()))
+    ops.append(gen.Gate((0,), gen.gate_y(), (3,), (0,)))
+    for g in ops:
+        s.apply_gate(g)
+        orc.apply(ref, g)
+    assert_amps(host(psi), ref, name, "structured")
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("n,k,c", [(1, 1, 0), (2, 2, 0), (2, 1, 1), (3, 2, 1), (6, 6, 0), (7, 6, 1), (7, 6, 0),
+                                   (8, 5, 3), (5, 4, 1), (4, 3, 0)])
+def test_edge_sizes(env, name, n, k, c):
+    rng = gen.rng_for(1000 + 10 * n + k + c)
+    init = gen.random_state(n, n + k + c)
+    ref = init.copy()
+    psi, s = make_state(env, n, name, init)
+    for _ in range(4):
+        qs = [int(x) for x in rng.choice(n, k + c, replace=False)]
+        m = gen.random_gate_dense(rng, k)
+        cv = [int(v) for v in rng.integers(0, 2, size=c)]
+        s.apply(qs[:k], m, qs[k:], cv)
+        orc.apply_gate(ref, qs[:k], m, qs[k:], cv)
+    assert_amps(host(psi), ref, name, f"n={n} k={k} c={c}")
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_pauli_expectations(env, name):
+    n = 12
+    rng = gen.rng_for(55)
+    init = gen.random_state(n, 55)
+    psi, s = make_state(env, n, name, init)
+    paulis, sites = gen.random_pauli_strings(n, 40, rng)
+    extra = np.zeros((8, n), dtype=np.int32)
+    extra[1, 0] = 1                 # X on qubit 0 only (partner in the same 16-byte unit)
+    extra[2, :] = 2                 # all Y
+    extra[3, :] = 3                 # all Z
+    extra[4, 1] = 2                 # Y on qubit 1
+    extra[5, [0, 5, 11]] = [2, 1, 3]
+    extra[6, n - 1] = 1
+    extra[7, [0, 1]] = [1, 1]
+    paulis = np.vstack([paulis, extra])
+    sites = np.tile(np.arange(n, dtype=np.int32), (paulis.shape[0], 1))
+    got = s.expectation_pauli(paulis, sites)
+    ref_state = host(psi)   # the state as stored in this precision
+    want = np.array([orc.expect_pauli(ref_state, p, q).real for p, q in zip(paulis, sites)])
+    assert_exp(got, want, name, "pauli")
+    # a subset of sites, in shuffled order
+    sub = np.array([[7, 2, 9]], dtype=np.int32)
+    ps = np.array([[2, 1, 3]], dtype=np.int32)
+    assert_exp(s.expectation_pauli(ps, sub), [orc.expect_pauli(ref_state, ps[0], sub[0]).real], name, "subset")
+    # the empty string is the norm
+    e = s.expectation_pauli(np.zeros((1, 0), np.int32), np.zeros((1, 0), np.int32))
+    assert abs(e[0] - orc.norm2(ref_state)) <= EXP_TOL[name]
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_measurement_probabilities_and_collapse(env, name):
+    n = 14
+    psi, s = make_state(env, n, name)
+    s.apply_circuit(gen.ghz_circuit(n))
+    p0, p1 = s.measure_probs([5])
+    assert abs(p0 - 0.5) <= EXP_TOL[name] and abs(p1 - 0.5) <= EXP_TOL[name]
+    p0, p1 = s.measure_probs([2, 9])
+    assert abs(p0 - 1) <= EXP_TOL[name] and p1 <= EXP_TOL[name]
+    out = s.measure([3], 0.75, collapse=True)
+    assert out == 1
+    v = host(psi)
+    assert abs(abs(v[-1]) - 1) <= AMP_TOL[name] and np.max(np.abs(v[:-1])) <= AMP_TOL[name]
+    # random state: probabilities, measurement outcome and collapse vs the oracle
+    init = gen.random_state(n, 77)
+    psi, s = make_state(env, n, name, init)
+    ref = host(psi)
+    rng = gen.rng_for(78)
+    for m in (1, 2, 5):
+        qs = [int(x) for x in rng.choice(n, m, replace=False)]
+        p0, p1 = s.measure_probs(qs)
+        w0, w1 = orc.parity_probs(ref, qs)
+        assert_exp([p0, p1], [w0, w1], name, "probs")
+    qs = [1, 6, 13]
+    r = 0.37
+    out = s.measure(qs, r, collapse=True)
+    want = orc.measure(ref, qs, r, collapse=True)
+    assert out == want
+    assert_amps(host(psi), ref, name, "collapse")
+    assert abs(s.norm2() - 1) <= EXP_TOL[name]
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("width", [2, 3, 4, 5, 6])
+def test_fused_native_matches_unfused_oracle(env, name, width):
+    n = 13
+    gates = gen.circuit_config2(n=n, layers=10, seed=9) + gen.circuit_config1(n=n, depth=3, seed=10)
+    ref = orc.run_circuit(gates, n)
+    psi, s = make_state(env, n, name)
+    nf = s.apply_fused(gates, width)
+    assert nf < len(gates)
+    assert_amps(host(psi), ref, name, f"fused w={width}")
+
+
+def test_full_size_28q_first_layer_sampled(env):
+    """The 28-qubit complex64 benchmark circuit, first layer (42 gates), in the
+    launch configuration the benchmark times; every amplitude is compared."""
+    n = 28
+    gates = gen.circuit_config1()[:42]
+    ref = orc.run_circuit(gates, n)
+    psi, s = make_state(env, n, "c64")
+    s.apply_circuit(gates)
+    got = psi.cpu().numpy()
+    err = 0.0
+    for a in range(0, 1 << n, 1 << 24):
+        err = max(err, float(np.max(np.abs(got[a:a + (1 << 24)].astype(np.complex128) - ref[a:a + (1 << 24)]))))
+    assert err <= AMP_TOL["c64"], err
+    z = s.expectation_pauli(np.array([[3], [3], [3]], np.int32), np.array([[0], [13], [27]], np.int32))
+    want = [orc.expect_pauli(ref, [3], [q]).real for q in (0, 13, 27)]
+    assert_exp(z, want, "c64", "28q <Z>")
+
+
+def test_full_size_28q_echo(env):
+    """The whole 28-qubit depth-40 circuit followed by its inverse returns |0...0>:
+    a property that holds at any size (norm preserved, amplitude 0 back to 1)."""
+    n = 28
+    gates = gen.circuit_config1()
+    psi, s = make_state(env, n, "c64")
+    s.apply_circuit(gates)
+    assert abs(s.norm2() - 1) < 1e-4
+    for g in reversed(gates):
+        s.apply_gate(g, adjoint=True)
+    a0 = complex(psi[0].item())
+    assert abs(a0 - 1) < 1e-4, a0
+    assert abs(s.norm2() - 1) < 1e-4
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_reductions_are_deterministic(env, name):
+    n = 20
+    init = gen.random_state(n, 5)
+    psi, s = make_state(env, n, name, init)
+    paulis, sites = gen.random_pauli_strings(n, 12, gen.rng_for(6))
+    a = s.expectation_pauli(paulis, sites)
+    b = s.expectation_pauli(paulis, sites)
+    assert np.array_equal(a, b)
+    assert s.measure_probs([3, 17]) == s.measure_probs([3, 17])
+    ref = host(psi)
+    want = np.array([orc.expect_pauli(ref, p, q).real for p, q in zip(paulis, sites)])
+    assert_exp(a, want, name, "n=20")
+
+
+def test_invalid_arguments_are_rejected(env):
+    torch, sv = env
+    psi, s = make_state(env, 5, "c64")
+    bad = [
+        lambda: s.apply([5], np.eye(2)),
+        lambda: s.apply([1, 1], np.eye(4)),
+        lambda: s.apply([0], np.eye(2), [0]),
+        lambda: s.apply([0], np.eye(2), [1], [2]),
+        lambda: s.expectation_pauli(np.array([[1, 1]]), np.array([[2, 2]])),
+        lambda: s.expectation_pauli(np.array([[4]]), np.array([[0]])),
+        lambda: s.measure_probs([]),
+        lambda: s.collapse([0], 0, 0.0),
+        lambda: s.measure([0], 1.0),
+    ]
+    for f in bad:
+        with pytest.raises(sv.SvError) as ei:
+            f()
+        assert ei.value.code == 1
+    big = gen.Gate(tuple(range(5)), gen.random_gate_dense(gen.rng_for(1), 5))
+    psi2, s2 = make_state(env, 6, "c128")
+    with pytest.raises(sv.SvError) as ei:
+        s2.apply_fused([big], 5, sv.SV_PREC_TF32)
+    assert ei.value.code == 2
+    n0 = s.launches()
+    s.apply([0], gen.gate_h())
+    assert s.launches() == n0 + 1
+    s.check()
