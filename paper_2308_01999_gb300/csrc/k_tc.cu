@@ -1,13 +1,478 @@
-// k_tc.cu -- fused 6-qubit gate application on the tensor cores (placeholder
-// until the tcgen05 kernel lands: reports the path as unsupported).
+// k_tc.cu -- fused 6-qubit gate application on the 5th-generation tensor cores
+// (tcgen05, TMEM accumulators). Sec. II-B: gate fusion turns many small
+// memory-bound gates into one 2^k x 2^k product; beyond k = 5 (complex64) the
+// product is compute-bound on CUDA cores, so here it runs on the tensor cores.
+//
+// The product. View the state as 64 x 2^(n-6): column c holds the 64 members
+// of group c (the amplitudes whose non-target bits spell c). With x_c the 128
+// reals (re, im interleaved: K index 2j + e for member j) of column c,
+//   out_c = A x_c,  A[2j+e][2l+f] = the real 2x2 block [[Re, -Im], [Im, Re]] of G[j][l],
+// so one fused gate is the real GEMM  D(128 x N) = A(128 x 128) * B(128 x N)
+// with B's columns the state columns. A is the same for every column.
+//
+// Precision: TF32 (operands rounded to nearest TF32, FP32 accumulation) or
+// split BF16 (x = hi + lo with hi, lo BF16; A*B ~ Ahi*Bhi + Ahi*Blo + Alo*Bhi,
+// three MMAs into one FP32 accumulator).
+//
+// Kernel structure (one persistent CTA per SM, 416 threads):
+//   warps 0-7   producers: gather a tile of 128 columns x 64 members from HBM
+//               (8-byte loads, consecutive lanes on consecutive columns), round
+//               or split, and store it to shared memory in the canonical K-major
+//               128-byte-swizzled operand layout; two tile buffers;
+//   warp 12     MMA issuer: one thread issues tcgen05.mma (M = N = 128) into one
+//               of two TMEM accumulators and commits to mbarriers;
+//   warps 8-11  epilogue: tcgen05.ld of the accumulator rows (warp w reads TMEM
+//               lanes 32*(w%4)..+31), pair up the (re, im) rows of each member
+//               with one shuffle, and store back in place.
+// A (the gate) is staged once per CTA from a host-built image of its swizzled
+// shared-memory layout. Every mbarrier wait is bounded by a clock budget; on
+// expiry the kernel records an error code in the device status word, drains
+// its own MMAs (again bounded), frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <vector>
+
 #include "sv_internal.h"
 
 namespace svk {
+namespace {
 
-bool tc6_supported(int, const int *) { return false; }
+constexpr int kNT = 128;              // columns per tile (MMA N)
+constexpr int kProdWarps = 8;
+constexpr int kMmaWarp = 12;
+constexpr int kThreadsTC = 13 * 32;
+constexpr int kProd = kProdWarps * 32;
+constexpr int kAImg = 64 * 1024;      // bytes of the A image (either precision)
+constexpr int kBStage = 64 * 1024;    // bytes of one B tile (either precision)
+constexpr int kTmemCols = 2 * kNT;    // two accumulators
+constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+constexpr int kErrTimeout = 0x7c01;
 
-cudaError_t launch_tc6(const LaunchCtx &, void *, int, const int *, const double *, sv_precision_t, void *, int *) {
-    return cudaErrorNotSupported;
+enum Prec { TF32 = 1, BF16 = 2 };
+
+struct TcSmem {
+    unsigned long long full[2], empty[2], acc_full[2], acc_empty[2], done;
+    unsigned tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false on timeout or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag, int *d_err) {
+    const long long t0 = clock64();
+    while (!mbar_try(a, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            atomicExch(d_err, kErrTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading byte offset
+// (unused for swizzled K-major, set to 16 B), stride byte offset 1024 B (eight
+// 128-byte rows), descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= 1ull << 46;
+    d |= 2ull << 61;
+    return d;
+}
+
+// Instruction descriptor: D = F32, A/B format (TF32 = 2, BF16 = 1), both K-major,
+// N = 128 (bits 17-22 hold N >> 3), M = 128 (bits 24-28 hold M >> 4).
+template <int P> __host__ __device__ constexpr uint32_t idesc() {
+    return (1u << 4) | ((P == TF32 ? 2u : 1u) << 7) | ((P == TF32 ? 2u : 1u) << 10) | ((uint32_t)(kNT >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int P>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    if constexpr (P == TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc<P>()), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc<P>()), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// (hi, lo) BF16 pairs of (a, b), packed with a in the low half
+__device__ __forceinline__ void split_bf16(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+struct TcGeom {
+    int pos[6];          // target positions, ascending
+    uint64_t off[64];    // member offsets
+    uint64_t n_cols;     // 2^(n-6)
+    uint64_t n_tiles;
+};
+
+__device__ __forceinline__ uint64_t col_base(uint64_t c, const TcGeom &G) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const uint64_t lo = c & ((1ull << G.pos[i]) - 1ull);
+        c = ((c ^ lo) << 1) | lo;
+    }
+    return c;
+}
+
+// byte offset of the 16-byte chunk `chunk` (0..7 within the 128-byte row) of
+// row r in K-block kb of an operand with `rows` rows (128-byte swizzle)
+__device__ __forceinline__ uint32_t sw128(int kb, int r, int chunk) {
+    return (uint32_t)(kb * (kNT * 128) + (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4));
+}
+
+template <int P, bool VEC4>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *__restrict__ d_err) {
+    extern __shared__ unsigned char smem_dyn[];
+    __shared__ TcSmem S;
+    // 1024-byte aligned operand area: A image, then two B stages
+    const uint32_t raw = smem_u32(smem_dyn);
+    const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
+    unsigned char *base = smem_dyn + pad;
+    unsigned char *sA = base;
+    unsigned char *sB0 = base + kAImg;     // stage s at sB0 + s * kBStage
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *abort_flag = &S.abort;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&S.full[i]), kProd);
+            mbar_init(smem_u32(&S.empty[i]), 1);
+            mbar_init(smem_u32(&S.acc_full[i]), 1);
+            mbar_init(smem_u32(&S.acc_empty[i]), 128);
+        }
+        mbar_init(smem_u32(&S.done), 1);
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // A image -> shared memory (plain copy; the host built the swizzled layout)
+    for (int i = threadIdx.x; i < kAImg / 16; i += kThreadsTC) reinterpret_cast<uint4 *>(sA)[i] = a_img[i];
+    fence_proxy_async();
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+    const uint64_t ntl = G.n_tiles;
+
+    if (warp < kProdWarps) {
+        // ---------------- producers ----------------
+        const int n = threadIdx.x & (kNT - 1);          // column within the tile
+        const int qhalf = threadIdx.x >> 7;             // member quads 8*qhalf .. 8*qhalf+7
+        int i = 0;
+        for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+            const int s = i & 1, u = i >> 1;
+            if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
+            const uint64_t c = t * kNT + n;
+            const bool valid = c < G.n_cols;
+            const uint64_t cb = valid ? col_base(c, G) : 0;
+            float2 v[32];
+#pragma unroll
+            for (int m = 0; m < 32; ++m) {
+                const int j = qhalf * 32 + m;
+                v[m] = valid ? sv[cb + G.off[j]] : make_float2(0.f, 0.f);
+            }
+            unsigned char *sb = sB0 + s * kBStage;
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq) {
+                const int q = qhalf * 8 + qq;     // members 4q .. 4q+3 = K 8q .. 8q+7
+                const float2 a0 = v[4 * qq], a1 = v[4 * qq + 1], a2 = v[4 * qq + 2], a3 = v[4 * qq + 3];
+                if constexpr (P == TF32) {
+                    const int kb = q >> 2, ch = 2 * (q & 3);
+                    uint4 w0 = make_uint4(to_tf32(a0.x), to_tf32(a0.y), to_tf32(a1.x), to_tf32(a1.y));
+                    uint4 w1 = make_uint4(to_tf32(a2.x), to_tf32(a2.y), to_tf32(a3.x), to_tf32(a3.y));
+                    *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch)) = w0;
+                    *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch + 1)) = w1;
+                } else {
+                    const int kb = q >> 3, ch = q & 7;
+                    uint4 hi, lo;
+                    split_bf16(a0.x, a0.y, hi.x, lo.x);
+                    split_bf16(a1.x, a1.y, hi.y, lo.y);
+                    split_bf16(a2.x, a2.y, hi.z, lo.z);
+                    split_bf16(a3.x, a3.y, hi.w, lo.w);
+                    *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch)) = hi;
+                    *reinterpret_cast<uint4 *>(sb + kBStage / 2 + sw128(kb, n, ch)) = lo;
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&S.full[s]));
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t a_addr = smem_u32(sA);
+            int i = 0;
+            for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+                const int s = i & 1, a = i & 1, u = i >> 1;
+                if (!mbar_wait(smem_u32(&S.full[s]), u & 1, abort_flag, d_err)) break;
+                if (u >= 1 && !mbar_wait(smem_u32(&S.acc_empty[a]), (u - 1) & 1, abort_flag, d_err)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(a * kNT);
+                const uint32_t b_addr = smem_u32(sB0) + (uint32_t)(s * kBStage);
+                if constexpr (P == TF32) {
+                    // K = 128 in 16 steps of 8 (32 bytes); 4 steps per 128-byte K-block
+#pragma unroll
+                    for (int ks = 0; ks < 16; ++ks) {
+                        const uint32_t off = (uint32_t)((ks >> 2) * (kNT * 128) + (ks & 3) * 32);
+                        mma<P>(d_tmem, sdesc(a_addr + off), sdesc(b_addr + off), ks > 0);
+                    }
+                } else {
+                    // K = 128 in 8 steps of 16 (32 bytes); Ahi*Bhi + Ahi*Blo + Alo*Bhi
+                    const uint32_t a_lo = a_addr + kAImg / 2, b_lo = b_addr + kBStage / 2;
+#pragma unroll
+                    for (int ks = 0; ks < 8; ++ks) {
+                        const uint32_t off = (uint32_t)((ks >> 2) * (kNT * 128) + (ks & 3) * 32);
+                        mma<P>(d_tmem, sdesc(a_addr + off), sdesc(b_addr + off), ks > 0);
+                        mma<P>(d_tmem, sdesc(a_addr + off), sdesc(b_lo + off), 1);
+                        mma<P>(d_tmem, sdesc(a_lo + off), sdesc(b_addr + off), 1);
+                    }
+                }
+                mma_commit(smem_u32(&S.empty[s]));
+                mma_commit(smem_u32(&S.acc_full[a]));
+            }
+            // drain: every MMA issued above has completed once `done` flips
+            mma_commit(smem_u32(&S.done));
+            const long long t0 = clock64();
+            while (!mbar_try(smem_u32(&S.done), 0) && clock64() - t0 < kWaitCycles) {
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue ----------------
+        const int sub = warp & 3;                   // TMEM lanes 32*sub .. 32*sub+31
+        const int m = sub * 32 + lane;              // accumulator row = 2j + e
+        const int j = m >> 1, e = m & 1;
+        const uint64_t offj = G.off[j];
+        int i = 0;
+        for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+            const int a = i & 1, u = i >> 1;
+            if (!mbar_wait(smem_u32(&S.acc_full[a]), u & 1, abort_flag, d_err)) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int cc = 0; cc < kNT / 32; ++cc) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * kNT + cc * 32), v);
+                const uint64_t c0 = t * kNT + (uint64_t)cc * 32;
+                if constexpr (VEC4) {
+                    // columns c..c+3 are adjacent amplitudes: the even lane stores
+                    // (c, c+1), the odd lane (c+2, c+3), 16 bytes each
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float s0 = e ? v[4 * q] : v[4 * q + 2];
+                        const float s1 = e ? v[4 * q + 1] : v[4 * q + 3];
+                        const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1);
+                        const float r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+                        const uint64_t col = c0 + 4 * q + (e ? 2 : 0);
+                        if (col < G.n_cols) {
+                            const float4 o = e ? make_float4(r0, v[4 * q + 2], r1, v[4 * q + 3])
+                                               : make_float4(v[4 * q], r0, v[4 * q + 1], r1);
+                            *reinterpret_cast<float4 *>(sv + col_base(col, G) + offj) = o;
+                        }
+                    }
+                } else {
+                    // any target layout: the even lane stores column c, the odd lane c+1
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float snd = e ? v[2 * q] : v[2 * q + 1];
+                        const float r = __shfl_xor_sync(0xffffffffu, snd, 1);
+                        const uint64_t col = c0 + 2 * q + e;
+                        if (col < G.n_cols) {
+                            const float2 o = e ? make_float2(r, v[2 * q + 1]) : make_float2(v[2 * q], r);
+                            sv[col_base(col, G) + offj] = o;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&S.acc_empty[a]));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kMmaWarp)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// ---------------- host: operand image of A ----------------
+uint32_t host_tf32(float x) {
+    // round to nearest (ties away from zero) to a 10-bit mantissa, as cvt.rna.tf32.f32
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u & 0xffffe000u;
+    u += 0x1000u;
+    return u & 0xffffe000u;
+}
+
+uint16_t host_bf16(float x) {
+    // round to nearest even
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_to_float(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+size_t host_sw128(int kb, int r, int chunk) {
+    return (size_t)kb * (128 * 128) + (size_t)(r >> 3) * 1024 + (size_t)(r & 7) * 128 + (size_t)((chunk ^ (r & 7)) << 4);
+}
+
+// A[2j+e][2l+f] from G (64x64 complex, row-major, interleaved doubles)
+double a_real(const double *g, int m, int k) {
+    const int j = m >> 1, e = m & 1, l = k >> 1, f = k & 1;
+    const double re = g[2 * (j * 64 + l)], im = g[2 * (j * 64 + l) + 1];
+    if (e == 0) return f == 0 ? re : -im;
+    return f == 0 ? im : re;
+}
+
+std::vector<unsigned char> build_a_image(const double *g, sv_precision_t prec) {
+    std::vector<unsigned char> img(kAImg, 0);
+    for (int m = 0; m < 128; ++m)
+        for (int k = 0; k < 128; ++k) {
+            const float x = (float)a_real(g, m, k);
+            if (prec == SV_PREC_TF32) {
+                const uint32_t w = host_tf32(x);
+                std::memcpy(&img[host_sw128(k >> 5, m, (k & 31) >> 2) + (k & 3) * 4], &w, 4);
+            } else {
+                const uint16_t hi = host_bf16(x);
+                const uint16_t lo = host_bf16(x - bf16_to_float(hi));
+                const size_t o = host_sw128(k >> 6, m, (k & 63) >> 3) + (k & 7) * 2;
+                std::memcpy(&img[o], &hi, 2);
+                std::memcpy(&img[kAImg / 2 + o], &lo, 2);
+            }
+        }
+    return img;
+}
+
+template <int P, bool VEC4>
+cudaError_t run_tc(const LaunchCtx &L, float2 *sv, const TcGeom &G, const uint4 *d_a, int *d_err) {
+    auto kern = k_tc6<P, VEC4>;
+    const int smem = kAImg + 2 * kBStage + 1024;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    uint64_t grid = (uint64_t)L.num_sms;
+    if (grid > G.n_tiles) grid = G.n_tiles;
+    kern<<<(unsigned)grid, kThreadsTC, smem, L.stream>>>(sv, G, d_a, d_err);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc6_supported(int n, const int *tpos) {
+    if (n < 6 || n > SV_MAX_QUBITS) return false;
+    for (int i = 0; i < 6; ++i)
+        if (tpos[i] < 0 || tpos[i] >= n || (i > 0 && tpos[i] <= tpos[i - 1])) return false;
+    return true;
+}
+
+cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, const double *mat, sv_precision_t prec,
+                       void *d_a, int *d_err) {
+    if (!tc6_supported(n, tpos) || (prec != SV_PREC_TF32 && prec != SV_PREC_SPLIT_BF16)) return cudaErrorInvalidValue;
+    TcGeom G{};
+    for (int i = 0; i < 6; ++i) G.pos[i] = tpos[i];
+    for (int j = 0; j < 64; ++j) {
+        uint64_t o = 0;
+        for (int t = 0; t < 6; ++t)
+            if ((j >> t) & 1) o |= 1ull << tpos[t];
+        G.off[j] = o;
+    }
+    G.n_cols = 1ull << (n - 6);
+    G.n_tiles = (G.n_cols + kNT - 1) / kNT;
+    const std::vector<unsigned char> img = build_a_image(mat, prec);
+    cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
+    if (e != cudaSuccess) return e;
+    const bool vec4 = tpos[0] >= 2;
+    float2 *s = reinterpret_cast<float2 *>(sv);
+    const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
+    if (prec == SV_PREC_TF32) return vec4 ? run_tc<TF32, true>(L, s, G, a, d_err) : run_tc<TF32, false>(L, s, G, a, d_err);
+    return vec4 ? run_tc<BF16, true>(L, s, G, a, d_err) : run_tc<BF16, false>(L, s, G, a, d_err);
 }
 
 }  // namespace svk
