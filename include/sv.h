@@ -156,6 +156,33 @@ SV_API sv_status_t sv_fuse_plan(const sv_gate_t *gates, int n_gates, int n_qubit
 SV_API sv_status_t sv_expectation_pauli(sv_handle_t h, const int *paulis, const int *sites,
                                  int n_sites, int n_strings, double *out);
 
+#define SV_NOALLOC_MAX_STRINGS 4096  /* strings per sv_expectation_pauli_noalloc call */
+
+/* Pauli-string expectation values without a handle and without allocating
+ * anything (this entry point has no counterpart in the paper). It is for
+ * callers that cannot call cudaMalloc: a process whose device memory is
+ * already owned by another allocator (for example a framework's caching
+ * allocator, or a memory pool sized to the whole GPU), where a new allocation
+ * would fail or force that allocator to give memory back, and latency-critical
+ * loops that cannot afford cudaMalloc/cudaFree, which may synchronise the
+ * device. Results equal sv_expectation_pauli's for the same state and strings.
+ * d_state: device memory, 2^n_qubits amplitudes of `dtype`, 16-byte aligned,
+ * caller-owned; stream: a cudaStream_t (NULL = legacy default stream); paulis,
+ * sites, n_sites, n_strings, out: as sv_expectation_pauli (out is host memory).
+ * Scratch space is one file-scope device array of 160 KiB that every GPU which
+ * loads the library holds until the process exits; at most
+ * SV_NOALLOC_MAX_STRINGS strings per call (more: SV_ERR_INSUFFICIENT_WORKSPACE,
+ * before any work is enqueued). The first call on a device, made with that
+ * device current, looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it: make that first call before any stream capture. All calls
+ * share the array: calls whose work overlaps on the GPU race, so the caller
+ * must order them (one stream, or synchronise between them). Synchronises the
+ * stream. Errors: INVALID_ARGUMENT as sv_expectation_pauli, or for a NULL or
+ * misaligned d_state or a bad dtype; CUDA. */
+SV_API sv_status_t sv_expectation_pauli_noalloc(int n_qubits, sv_dtype_t dtype, const void *d_state, void *stream,
+                                                const int *paulis, const int *sites, int n_sites, int n_strings,
+                                                double *out);
+
 /* Probabilities of a measurement in the Z-product basis of `qubits` (Table I,
  * "Measurement"): p_even/p_odd = sum of |psi_i|^2 over basis states whose
  * measured bits have even/odd parity, in FP64. Synchronises the stream. */

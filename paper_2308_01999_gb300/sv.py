@@ -38,7 +38,7 @@ EXPORTED = [
     "sv_create", "sv_destroy", "sv_set_stream", "sv_set_state_pointer", "sv_set_basis_state",
     "sv_copy_from_host", "sv_copy_to_host", "sv_apply_matrix", "sv_apply_fused", "sv_fuse_plan",
     "sv_expectation_pauli", "sv_measure_probs", "sv_collapse", "sv_measure", "sv_norm2",
-    "sv_check_device_status", "sv_launch_count", "sv_status_string",
+    "sv_check_device_status", "sv_launch_count", "sv_status_string", "sv_expectation_pauli_noalloc",
 ]
 
 
@@ -80,6 +80,7 @@ def lib():
             "sv_measure": [_VP, _I, C.c_int, C.c_double, C.c_int, _I],
             "sv_norm2": [_VP, _D], "sv_check_device_status": [_VP],
             "sv_launch_count": [_VP, C.POINTER(C.c_uint64)],
+            "sv_expectation_pauli_noalloc": [C.c_int, C.c_int, _VP, _VP, _I, _I, C.c_int, C.c_int, _D],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -217,6 +218,23 @@ def sv_expectation_pauli(h: int, paulis, sites) -> np.ndarray:
     out = np.zeros(p.shape[0], dtype=np.float64)
     _check(lib().sv_expectation_pauli(_VP(h), p.ctypes.data_as(_I), s.ctypes.data_as(_I), int(p.shape[1]),
                                       int(p.shape[0]), out.ctypes.data_as(_D)), "sv_expectation_pauli")
+    return out
+
+
+def sv_expectation_pauli_noalloc(n_qubits: int, dtype: int, d_state_ptr: int, stream_ptr: int, paulis,
+                                 sites) -> np.ndarray:
+    """Allocation-free Pauli expectations on a caller-owned device state (no handle)."""
+    p = np.ascontiguousarray(np.asarray(paulis, dtype=np.int32))
+    s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
+    if p.ndim == 1:
+        p, s = p[None, :], s[None, :]
+    if p.shape != s.shape:
+        raise ValueError("paulis and sites must have the same shape")
+    out = np.zeros(p.shape[0], dtype=np.float64)
+    _check(lib().sv_expectation_pauli_noalloc(int(n_qubits), int(dtype), _VP(d_state_ptr), _VP(stream_ptr),
+                                              p.ctypes.data_as(_I), s.ctypes.data_as(_I), int(p.shape[1]),
+                                              int(p.shape[0]), out.ctypes.data_as(_D)),
+           "sv_expectation_pauli_noalloc")
     return out
 
 
