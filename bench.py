@@ -151,6 +151,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(vals, device=None):
+    """Element-wise maximum of `vals` over all ranks (identity without a process
+    group); the step time of a replica job is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def job_throughput(bytes_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job GB/s of `world` independent replicas, timed by the slowest rank."""
+    return world * bytes_per_rank / (max_ms * 1e-3) / 1e9
+
+
 def cpu_baseline(gates, budget_s: float = 12.0):
     """The CPU oracle (complex128, OpenMP) on the first gates of the same circuit
     at the same size, until `budget_s` of CPU work; value in the metric's unit
@@ -295,10 +312,7 @@ def run_ours(args):
         barrier()
         e2e_ms = e0.elapsed_time(e1) / e_steps
 
-    if world > 1:
-        t = torch.tensor([ms, e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -321,7 +335,7 @@ def run_ours(args):
             t = np.mean([per_gate_ms[i] / args.steps for i in idx])
             per_kind[kind] = round(gate_bytes(gates[idx[0]]) / (t * 1e-3) / 1e9, 1)
     gates_ms = sum(per_gate_ms.values()) / args.steps
-    value = world * nbytes / (ms * 1e-3) / 1e9
+    value = job_throughput(nbytes, world, ms)
     cpu = cpu_baseline(gates) if world == 1 and not args.no_cpu_baseline else None
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
@@ -343,7 +357,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": su2_bytes, "avg_launch_ms": round(avg_su2, 4)},
         "per_target_gbs": per_target, "per_kind_gbs": per_kind,
         "gpu_launches": int(launches),
-        "e2e": {"value": round(world * nbytes / (e2e_ms * 1e-3) / 1e9, 1), "unit": UNIT,
+        "e2e": {"value": round(job_throughput(nbytes, world, e2e_ms), 1), "unit": UNIT,
                 "h2d_bytes_per_step": AMP_BYTES << N_QUBITS, "d2h_bytes_per_step": AMP_BYTES << N_QUBITS,
                 "ms_per_step": round(e2e_ms, 3)},
         "clocks": clk,
@@ -355,6 +369,192 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_fused(args):
+    """The 32-qubit brick-wall circuit (40 layers of Haar SU(2) + CZ wall, 1900
+    gates) on a 32 GiB complex64 state: greedy fusion to 5- and 6-qubit blocks
+    applied on the tensor cores (TF32, split BF16) or on CUDA cores (native),
+    against the unfused complex64 run, with errors measured against an unfused
+    complex128 run of the same circuit (64 GiB). Per-block kernel times come
+    from CUDA events around each block's launch on the handle's stream."""
+    import torch
+
+    from paper_2308_01999_gb300 import sv
+
+    n = args.fused_qubits
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    gates = gen.circuit_config2(n, 40, seed=2)
+    stream = torch.cuda.Stream(dev)
+    state_bytes = 2 * AMP_BYTES * (1 << n)          # read + write of the c64 state
+    peak_hbm, _ = load_peaks()
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        bf16_peak = float(json.load(f)["bf16_tflops"])
+    tf32_peak = bf16_peak * 1.1 / 2.25              # nominal dense TF32 : BF16 ratio
+    out = {"workload": f"{n}-qubit brick wall, 40 layers, {len(gates)} gates, complex64", "n_qubits": n}
+
+    def event_pair():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    ref = None
+    with torch.cuda.stream(stream):
+        if not args.no_ref:
+            ref = torch.empty(1 << n, dtype=torch.complex128, device=dev)
+            r = sv.StateVector(ref, stream)
+            r.set_basis_state(0)
+            e0, e1 = event_pair()
+            e0.record(stream)
+            r.apply_circuit(gates)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out["c128_unfused_s"] = round(e0.elapsed_time(e1) / 1e3, 3)
+            ref_z = r.expectation_z_all()
+            r.close()
+        psi = torch.empty(1 << n, dtype=torch.complex64, device=dev)
+        s = sv.StateVector(psi, stream)
+
+        def errors():
+            if ref is None:
+                return {}
+            num, den, mx = 0.0, 0.0, 0.0
+            chunk = 1 << 27
+            for a in range(0, 1 << n, chunk):
+                d = psi[a:a + chunk].to(torch.complex128) - ref[a:a + chunk]
+                num += float(torch.sum(torch.abs(d) ** 2))
+                den += float(torch.sum(torch.abs(ref[a:a + chunk]) ** 2))
+                mx = max(mx, float(torch.max(torch.abs(d))))
+            z = s.expectation_z_all()
+            return {"rel_l2": num ** 0.5 / den ** 0.5, "max_abs": mx, "max_abs_z": float(np.max(np.abs(z - ref_z)))}
+
+        s.set_basis_state(0)
+        e0, e1 = event_pair()
+        e0.record(stream)
+        s.apply_circuit(gates)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["unfused_c64"] = {"s": round(e0.elapsed_time(e1) / 1e3, 3), "launches": len(gates), **errors()}
+
+        precs = {"tf32": sv.SV_PREC_TF32, "bf16": sv.SV_PREC_SPLIT_BF16, "native": sv.SV_PREC_NATIVE}
+        for w in [int(x) for x in args.widths.split(",")]:
+            plan = sv.sv_fuse_plan(gates, n, w)
+            blocks = [gen.Gate(tuple(t), m) for t, m in plan]
+            for prec_name in args.precs.split(","):
+                prec = precs[prec_name]
+                s.set_basis_state(0)
+                torch.cuda.synchronize()
+                evs = [event_pair() for _ in blocks]
+                t0, t1 = event_pair()
+                t0.record(stream)
+                for b, (a, z) in zip(blocks, evs):
+                    a.record(stream)
+                    s.apply_fused([b], 6, prec)
+                    z.record(stream)
+                t1.record(stream)
+                torch.cuda.synchronize()
+                s.check()
+                per = [a.elapsed_time(z) for a, z in evs]
+                big = [ms for b, ms in zip(blocks, per) if b.k >= 5]
+                rec = {"blocks": len(blocks), "blocks_5_6": len(big), "s": round(t0.elapsed_time(t1) / 1e3, 3),
+                       "kernel_s": round(sum(per) / 1e3, 3)}
+                if big:
+                    avg = sum(big) / len(big)
+                    rec["avg_block_ms"] = round(avg, 3)
+                    rec["block_gbs"] = round(state_bytes / (avg * 1e-3) / 1e9, 1)
+                    rec["hbm_frac"] = round(state_bytes / (avg * 1e-3) / 1e9 / peak_hbm, 4)
+                    if prec_name != "native":
+                        flop = 2 * 128 * 128 * (1 << (n - 6)) * (3 if prec_name == "bf16" else 1)
+                        rec["tensor_tflops"] = round(flop / (avg * 1e-3) / 1e12, 1)
+                        pk = bf16_peak if prec_name == "bf16" else tf32_peak
+                        rec["tensor_frac"] = round(flop / (avg * 1e-3) / 1e12 / pk, 4)
+                if big and prec_name != "native":
+                    # per-block time by the lowest and the highest target qubit
+                    by_lo, by_hi = {}, {}
+                    for blk, ms in zip(blocks, per):
+                        if blk.k >= 5:
+                            by_lo.setdefault(min(blk.targets), []).append(ms)
+                            by_hi.setdefault(max(blk.targets), []).append(ms)
+                    rec["ms_by_lowest_target"] = {str(q): round(float(np.mean(v)), 2) for q, v in sorted(by_lo.items())}
+                    rec["ms_by_highest_target"] = {str(q): round(float(np.mean(v)), 2) for q, v in sorted(by_hi.items())}
+                rec.update(errors())
+                out[f"w{w}_{prec_name}"] = rec
+                print(json.dumps({f"w{w}_{prec_name}": rec}), file=sys.stderr, flush=True)
+        s.close()
+    out["peaks"] = {"hbm_gbs": peak_hbm, "bf16_tflops": bf16_peak, "tf32_tflops_from_nominal_ratio": round(tf32_peak, 1)}
+    print(json.dumps(out))
+
+
+def run_batch(args):
+    """Many small states in one persistent launch: 4096 independent states with
+    qubit counts uniform on 10..20, each a hardware-efficient ansatz of 6 layers
+    (RY, RZ per qubit, CNOT ladder) followed by 8 random Pauli strings reduced in
+    FP64. The fusion width is picked by timing every width (the autotuner); the
+    plain engine -- one state at a time, one launch per gate, then the
+    expectation call -- runs on a sample of the same states for comparison."""
+    import torch
+
+    from paper_2308_01999_gb300 import sv
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t_gen = time.perf_counter()
+    work = gen.batched_ansatz_workload(count=args.batch_states, seed=3)
+    states = [(n, gates, paulis) for n, gates, paulis, _ in work]
+    t_gen = time.perf_counter() - t_gen
+    stream = torch.cuda.Stream(dev)
+    out = {"workload": f"{len(states)} states, qubits uniform 10..20, 6-layer ansatz, 8 Pauli strings each, complex64",
+           "gates": sum(len(g) for _, g, _ in states)}
+    with torch.cuda.stream(stream):
+        b = sv.Batch(stream)
+        tune = {}
+        best = None
+        buf = None
+        for w in (1, 2, 3, 4):
+            t0 = time.perf_counter()
+            info = b.compile(states, fusion_width=w)
+            comp = time.perf_counter() - t0
+            if buf is None:
+                buf = torch.empty(b.state_amps, dtype=torch.complex64, device=dev)
+            b.launch(buf)
+            b.results()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record(stream)
+            for _ in range(reps):
+                b.launch(buf)
+            e1.record(stream)
+            res = b.results()
+            ms = e0.elapsed_time(e1) / reps
+            tune[w] = {"ms": round(ms, 3), "states_per_s": round(len(states) / (ms * 1e-3), 1),
+                       "ops": info["ops"], "stages": info["stages"], "compile_s": round(comp, 2)}
+            if best is None or ms < tune[best]["ms"]:
+                best = w
+            print(json.dumps({"width": w, **tune[w]}), file=sys.stderr, flush=True)
+        out["autotune"] = tune
+        out["fusion_width"] = best
+        out["batched_states_per_s"] = tune[best]["states_per_s"]
+        out["batched_ms"] = tune[best]["ms"]
+        b.close()
+        # the plain engine on a sample of the same states
+        sample = states[: args.plain_sample]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for n, gates, paulis in sample:
+            psi = torch.empty(1 << n, dtype=torch.complex64, device=dev)
+            s = sv.StateVector(psi, stream)
+            s.set_basis_state(0)
+            s.apply_circuit(gates)
+            s.expectation_pauli(paulis, np.tile(np.arange(n, dtype=np.int32), (paulis.shape[0], 1)))
+            s.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        frac = sum(1 << n for n, _, _ in sample) / sum(1 << n for n, _, _ in states)
+        out["plain_sample_states"] = len(sample)
+        out["plain_states_per_s"] = round(len(sample) / dt, 1)
+        out["plain_est_full_s"] = round(dt / frac, 2)
+        out["speedup_vs_plain_per_state"] = round(out["batched_states_per_s"] / out["plain_states_per_s"], 1)
+    out["generation_s"] = round(t_gen, 1)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,11 +564,23 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--qubits", type=int, default=28,
                     help="state size; 28 is the benchmark workload, smaller sizes are for profiling captures")
+    ap.add_argument("--workload", choices=("circuit28", "fused32", "batch"), default="circuit28",
+                    help="fused32: the 32-qubit fused brick-wall study (tensor cores, errors vs complex128)")
+    ap.add_argument("--fused-qubits", type=int, default=32)
+    ap.add_argument("--no-ref", action="store_true", help="fused32 without the complex128 reference run")
+    ap.add_argument("--widths", default="5,6", help="fused32: fusion widths")
+    ap.add_argument("--batch-states", type=int, default=4096, help="batch: number of states")
+    ap.add_argument("--plain-sample", type=int, default=256, help="batch: states run through the plain engine")
+    ap.add_argument("--precs", default="tf32,bf16,native", help="fused32: precisions")
     args = ap.parse_args()
     global N_QUBITS
     N_QUBITS = args.qubits
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "fused32":
+        run_fused(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

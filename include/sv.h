@@ -209,6 +209,63 @@ SV_API sv_status_t sv_check_device_status(sv_handle_t h);
 /* Number of kernels this handle has launched since sv_create. */
 SV_API sv_status_t sv_launch_count(sv_handle_t h, uint64_t *out);
 
+/* ---- Batched small state vectors ----
+ * Many independent circuits on small states advanced by one persistent launch
+ * (gate application and expectation values of Table I, with gate fusion of
+ * Sec. II-B, on a batch). Each state of up to SV_BATCH_TILE_QUBITS qubits
+ * lives in GPU shared memory for its whole circuit; larger ones (up to
+ * SV_BATCH_MAX_QUBITS) are processed in passes over 2^14-amplitude tiles that
+ * each hold every gate of the pass. States start as |0...0>. complex64 only. */
+#define SV_BATCH_MAX_QUBITS 20
+#define SV_BATCH_TILE_QUBITS 14
+#define SV_BATCH_KEEP_STATES 1    /* flag: write every final state to d_states */
+
+typedef struct {
+    int n_qubits;           /* 1..SV_BATCH_MAX_QUBITS */
+    int gate_begin;         /* the state's gates: gates[gate_begin .. gate_begin + n_gates) */
+    int n_gates;
+    int pauli_begin;        /* its strings: n_strings rows of n_qubits codes (0=I,1=X,2=Y,3=Z) at
+                               paulis[pauli_begin + s * n_qubits + q], code for qubit q */
+    int n_strings;
+    int out_begin;          /* its expectation values: out[out_begin .. out_begin + n_strings) */
+    uint64_t state_offset;  /* amplitude offset of the state in d_states (2^n_qubits amplitudes) */
+} sv_batch_item_t;
+
+typedef struct sv_batch_ctx *sv_batch_t;
+
+/* Create / destroy a batch engine bound to a cudaStream_t (NULL = legacy
+ * default stream). Creation allocates nothing on the device; the first
+ * launch allocates a program buffer, which grows as needed and is freed by
+ * destroy. */
+SV_API sv_status_t sv_batch_create(void *stream, sv_batch_t *out);
+SV_API sv_status_t sv_batch_destroy(sv_batch_t b);
+
+/* Compile the batch on the host (no GPU work): per state, greedy fusion into
+ * blocks of at most fusion_width (1..4) qubits, exact structure analysis
+ * (controls, diagonal, generalized permutation, dense), and passes of at most
+ * 14 local qubits. Each gate: 1..4 targets, at most 8 controls, all qubits
+ * distinct and < n_qubits, targets + controls <= min(n_qubits, 14).
+ * Errors: INVALID_ARGUMENT for any bad field; NOT_SUPPORTED for a fused block
+ * the batch kernel cannot take. Replaces any previous program. */
+SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, int n_items,
+                                    const sv_gate_t *gates, int n_gates_total, const int *paulis,
+                                    int fusion_width);
+
+/* Sizes of the compiled program and the engine's launch count. Any pointer may be NULL. */
+SV_API sv_status_t sv_batch_info(sv_batch_t b, int *n_items, int *n_stages, int *n_ops,
+                                 uint64_t *state_amps, uint64_t *launches);
+
+/* Upload the program and enqueue the one persistent kernel. d_states: device
+ * memory of at least the largest state_offset + 2^n_qubits complex64
+ * amplitudes, 16-byte aligned, caller-owned; states above 14 qubits always use
+ * it, smaller ones only with SV_BATCH_KEEP_STATES. dtype must be SV_C64.
+ * Asynchronous. */
+SV_API sv_status_t sv_batch_launch(sv_batch_t b, sv_dtype_t dtype, void *d_states, int flags);
+
+/* Wait for the last launch and copy its expectation values (FP64, indexed by
+ * out_begin + s) to host memory `out` of at least n_out doubles. */
+SV_API sv_status_t sv_batch_results(sv_batch_t b, double *out, int n_out);
+
 /* A static description of a status code. */
 SV_API const char *sv_status_string(sv_status_t s);
 

@@ -14,16 +14,20 @@
 // split BF16 (x = hi + lo with hi, lo BF16; A*B ~ Ahi*Bhi + Ahi*Blo + Alo*Bhi,
 // three MMAs into one FP32 accumulator).
 //
-// Kernel structure (one persistent CTA per SM, 416 threads):
+// Kernel structure (one persistent CTA per SM, 544 threads):
 //   warps 0-7   producers: gather a tile of 128 columns x 64 members from HBM
 //               (8-byte loads, consecutive lanes on consecutive columns), round
 //               or split, and store it to shared memory in the canonical K-major
 //               128-byte-swizzled operand layout; two tile buffers;
-//   warp 12     MMA issuer: one thread issues tcgen05.mma (M = N = 128) into one
+//   warp 16     MMA issuer: one thread issues tcgen05.mma (M = N = 128) into one
 //               of two TMEM accumulators and commits to mbarriers;
-//   warps 8-11  epilogue: tcgen05.ld of the accumulator rows (warp w reads TMEM
-//               lanes 32*(w%4)..+31), pair up the (re, im) rows of each member
-//               with one shuffle, and store back in place.
+//   warps 8-15  epilogue: tcgen05.ld of the accumulator rows (warp w reads TMEM
+//               lanes 32*(w%4)..+31, columns of one half of the tile), pair up
+//               the (re, im) rows of each member with one shuffle, and store back
+//               in place (16-byte stores unless qubit 0 is a target).
+// Addresses: a tile starts at a multiple of 128 columns, so the amplitude
+// offset of column t*128 + i is col_base(t*128) | pd[i], with the deposit table
+// pd[] computed once per CTA.
 // A (the gate) is staged once per CTA from a host-built image of its swizzled
 // shared-memory layout. Every mbarrier wait is bounded by a clock budget; on
 // expiry the kernel records an error code in the device status word, drains
@@ -39,10 +43,12 @@ namespace svk {
 namespace {
 
 constexpr int kNT = 128;              // columns per tile (MMA N)
-constexpr int kProdWarps = 8;
-constexpr int kMmaWarp = 12;
-constexpr int kThreadsTC = 13 * 32;
+constexpr int kProdWarps = 8;         // warps 0..7
+constexpr int kEpiWarps = 8;          // warps 8..15: two per TMEM lane quarter, one per column half
+constexpr int kMmaWarp = kProdWarps + kEpiWarps;
+constexpr int kThreadsTC = (kMmaWarp + 1) * 32;
 constexpr int kProd = kProdWarps * 32;
+constexpr int kEpi = kEpiWarps * 32;
 constexpr int kAImg = 64 * 1024;      // bytes of the A image (either precision)
 constexpr int kBStage = 64 * 1024;    // bytes of one B tile (either precision)
 constexpr int kTmemCols = 2 * kNT;    // two accumulators
@@ -53,6 +59,7 @@ enum Prec { TF32 = 1, BF16 = 2 };
 
 struct TcSmem {
     unsigned long long full[2], empty[2], acc_full[2], acc_empty[2], done;
+    uint64_t pd[kNT];   // column offset i in a tile -> amplitude offset (bits deposited around the targets)
     unsigned tmem_base;
     int abort;
 };
@@ -212,12 +219,14 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
             mbar_init(smem_u32(&S.full[i]), kProd);
             mbar_init(smem_u32(&S.empty[i]), 1);
             mbar_init(smem_u32(&S.acc_full[i]), 1);
-            mbar_init(smem_u32(&S.acc_empty[i]), 128);
+            mbar_init(smem_u32(&S.acc_empty[i]), kEpi);
         }
         mbar_init(smem_u32(&S.done), 1);
         S.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // A tile starts at a multiple of kNT columns, so col_base(t*kNT + i) = col_base(t*kNT) | pd[i]
+    if (threadIdx.x < kNT) S.pd[threadIdx.x] = col_base((uint64_t)threadIdx.x, G);
     // A image -> shared memory (plain copy; the host built the swizzled layout)
     for (int i = threadIdx.x; i < kAImg / 16; i += kThreadsTC) reinterpret_cast<uint4 *>(sA)[i] = a_img[i];
     fence_proxy_async();
@@ -243,7 +252,7 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
             if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
             const uint64_t c = t * kNT + n;
             const bool valid = c < G.n_cols;
-            const uint64_t cb = valid ? col_base(c, G) : 0;
+            const uint64_t cb = valid ? (col_base(t * kNT, G) | S.pd[n]) : 0;
             float2 v[32];
 #pragma unroll
             for (int m = 0; m < 32; ++m) {
@@ -318,6 +327,7 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
     } else {
         // ---------------- epilogue ----------------
         const int sub = warp & 3;                   // TMEM lanes 32*sub .. 32*sub+31
+        const int half = (warp - kProdWarps) >> 2;  // columns 64*half .. 64*half+63 of the tile
         const int m = sub * 32 + lane;              // accumulator row = 2j + e
         const int j = m >> 1, e = m & 1;
         const uint64_t offj = G.off[j];
@@ -326,38 +336,59 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
             const int a = i & 1, u = i >> 1;
             if (!mbar_wait(smem_u32(&S.acc_full[a]), u & 1, abort_flag, d_err)) break;
             tc_fence_after();
+            const uint64_t tb = col_base(t * kNT, G) + offj;
+            const uint64_t tb2 = col_base(t * kNT, G) + G.off[(m >> 2) << 1];   // member 2p of this lane quad
+            const uint64_t tcol = t * kNT;
 #pragma unroll 1
-            for (int cc = 0; cc < kNT / 32; ++cc) {
+            for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * kNT + cc * 32), v);
-                const uint64_t c0 = t * kNT + (uint64_t)cc * 32;
                 if constexpr (VEC4) {
-                    // columns c..c+3 are adjacent amplitudes: the even lane stores
-                    // (c, c+1), the odd lane (c+2, c+3), 16 bytes each
+                    // qubit 0 is not a target, so columns c and c+1 (c even) are adjacent
+                    // amplitudes: the even lane stores (c, c+1), the odd lane (c+2, c+3)
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const float s0 = e ? v[4 * q] : v[4 * q + 2];
                         const float s1 = e ? v[4 * q + 1] : v[4 * q + 3];
                         const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1);
                         const float r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-                        const uint64_t col = c0 + 4 * q + (e ? 2 : 0);
-                        if (col < G.n_cols) {
+                        const int ci = cc * 32 + 4 * q + (e ? 2 : 0);
+                        if (tcol + ci < G.n_cols) {
                             const float4 o = e ? make_float4(r0, v[4 * q + 2], r1, v[4 * q + 3])
                                                : make_float4(v[4 * q], r0, v[4 * q + 1], r1);
-                            *reinterpret_cast<float4 *>(sv + col_base(col, G) + offj) = o;
+                            *reinterpret_cast<float4 *>(sv + (tb | S.pd[ci])) = o;
                         }
                     }
                 } else {
-                    // any target layout: the even lane stores column c, the odd lane c+1
+                    // qubit 0 is the lowest target: members 2p and 2p+1 of a column are
+                    // adjacent amplitudes, held by lanes 4p..4p+3 as (re, im, re, im)
+                    // rows. A 4x4 transpose within each lane quad (three rotations)
+                    // gives lane 4p+r column c+r's 16 bytes.
+                    const int r4 = lane & 3, qbase = lane & ~3;
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const float snd = e ? v[2 * q] : v[2 * q + 1];
-                        const float r = __shfl_xor_sync(0xffffffffu, snd, 1);
-                        const uint64_t col = c0 + 2 * q + e;
-                        if (col < G.n_cols) {
-                            const float2 o = e ? make_float2(r, v[2 * q + 1]) : make_float2(v[2 * q], r);
-                            sv[col_base(col, G) + offj] = o;
+                    for (int q = 0; q < 8; ++q) {
+                        const float own = r4 == 0 ? v[4 * q] : r4 == 1 ? v[4 * q + 1] : r4 == 2 ? v[4 * q + 2] : v[4 * q + 3];
+                        float t0v = own, t1v = 0.f, t2v = 0.f, t3v = 0.f;   // t_k = M[k][r4]
+#pragma unroll
+                        for (int sft = 1; sft < 4; ++sft) {
+                            // sender k sends M[k][(k - sft) & 3]; receiver r reads lane (r + sft) & 3
+                            const int ei = (r4 - sft) & 3;
+                            const float snd = ei == 0 ? v[4 * q] : ei == 1 ? v[4 * q + 1] : ei == 2 ? v[4 * q + 2] : v[4 * q + 3];
+                            const float got = __shfl_sync(0xffffffffu, snd, qbase + ((r4 + sft) & 3));
+                            const int k = (r4 + sft) & 3;   // the received value is M[k][r4]
+                            t0v = k == 0 ? got : t0v;
+                            t1v = k == 1 ? got : t1v;
+                            t2v = k == 2 ? got : t2v;
+                            t3v = k == 3 ? got : t3v;
                         }
+                        // own element M[r4][r4]
+                        t0v = r4 == 0 ? own : t0v;
+                        t1v = r4 == 1 ? own : t1v;
+                        t2v = r4 == 2 ? own : t2v;
+                        t3v = r4 == 3 ? own : t3v;
+                        const int ci = cc * 32 + 4 * q + r4;
+                        if (tcol + ci < G.n_cols)
+                            *reinterpret_cast<float4 *>(sv + (tb2 | S.pd[ci])) = make_float4(t0v, t1v, t2v, t3v);
                     }
                 }
             }
@@ -468,7 +499,7 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     const std::vector<unsigned char> img = build_a_image(mat, prec);
     cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
     if (e != cudaSuccess) return e;
-    const bool vec4 = tpos[0] >= 2;
+    const bool vec4 = tpos[0] >= 1;
     float2 *s = reinterpret_cast<float2 *>(sv);
     const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
     if (prec == SV_PREC_TF32) return vec4 ? run_tc<TF32, true>(L, s, G, a, d_err) : run_tc<TF32, false>(L, s, G, a, d_err);

@@ -13,6 +13,7 @@
 #include <new>
 #include <vector>
 
+#include "sv_classify.h"
 #include "sv_fuse.h"
 #include "sv_internal.h"
 
@@ -70,84 +71,9 @@ bool valid_qubits(int n, const int *targets, int k, const int *controls, int c) 
     return true;
 }
 
-// ---- exact structure analysis of a gate matrix ----
-
-struct Gate {
-    std::vector<int> t;      // targets, bit j of the matrix index is t[j]
-    std::vector<int> c;      // controls
-    std::vector<int> cv;     // control values
-    std::vector<cd> m;       // 2^k x 2^k row-major
-};
-
-int ins_bit(int a, int j, int b) {   // insert bit value b at position j of a
-    const int lo = a & ((1 << j) - 1);
-    return ((a >> j) << (j + 1)) | (b << j) | lo;
-}
-
-// If target bit j splits M into blocks with zero off-diagonal blocks and one
-// diagonal block equal to the identity, that bit acts as a control: return the
-// control value (1 if the bit-0 block is the identity) and the other block.
-int extract_control(const Gate &g, int j, std::vector<cd> &rest) {
-    const int k = (int)g.t.size(), D = 1 << k, H = D / 2;
-    for (int r = 0; r < D; ++r)
-        for (int c = 0; c < D; ++c)
-            if (((r >> j) & 1) != ((c >> j) & 1) && g.m[r * D + c] != cd(0)) return -1;
-    for (int val = 0; val < 2; ++val) {
-        bool ident = true;
-        for (int a = 0; a < H && ident; ++a)
-            for (int b = 0; b < H && ident; ++b)
-                if (g.m[ins_bit(a, j, val) * D + ins_bit(b, j, val)] != (a == b ? cd(1) : cd(0))) ident = false;
-        if (ident) {
-            rest.assign(H * H, cd(0));
-            for (int a = 0; a < H; ++a)
-                for (int b = 0; b < H; ++b) rest[a * H + b] = g.m[ins_bit(a, j, 1 - val) * D + ins_bit(b, j, 1 - val)];
-            return 1 - val;
-        }
-    }
-    return -1;
-}
-
-void simplify_controls(Gate &g) {
-    bool changed = true;
-    while (changed && !g.t.empty()) {
-        changed = false;
-        for (int j = 0; j < (int)g.t.size(); ++j) {
-            std::vector<cd> rest;
-            const int val = extract_control(g, j, rest);
-            if (val < 0) continue;
-            g.c.push_back(g.t[j]);
-            g.cv.push_back(val);
-            g.t.erase(g.t.begin() + j);
-            g.m.swap(rest);
-            changed = true;
-            break;
-        }
-    }
-}
-
-// matrix for targets sorted ascending (new bit i <-> old bit sigma[i])
-void sort_targets(Gate &g) {
-    const int k = (int)g.t.size(), D = 1 << k;
-    std::vector<int> sigma(k);
-    for (int i = 0; i < k; ++i) sigma[i] = i;
-    std::sort(sigma.begin(), sigma.end(), [&](int a, int b) { return g.t[a] < g.t[b]; });
-    bool ident = true;
-    for (int i = 0; i < k; ++i) ident &= sigma[i] == i;
-    if (ident) return;
-    auto old_index = [&](int rn) {
-        int ro = 0;
-        for (int i = 0; i < k; ++i)
-            if ((rn >> i) & 1) ro |= 1 << sigma[i];
-        return ro;
-    };
-    std::vector<cd> m2(D * D);
-    for (int r = 0; r < D; ++r)
-        for (int c = 0; c < D; ++c) m2[r * D + c] = g.m[old_index(r) * D + old_index(c)];
-    std::vector<int> t2(k);
-    for (int i = 0; i < k; ++i) t2[i] = g.t[sigma[i]];
-    g.t.swap(t2);
-    g.m.swap(m2);
-}
+using svc::Gate;
+using svc::simplify_controls;
+using svc::sort_targets;
 
 svk::GroupGeom make_geom(const std::vector<int> &inserted, const std::vector<int> &c, const std::vector<int> &cv) {
     svk::GroupGeom G{};
@@ -218,12 +144,14 @@ sv_status_t apply_gate(sv_ctx *h, Gate g, sv_precision_t prec) {
         buf[2 * i + 1] = g.m[i].imag();
     }
     if (prec != SV_PREC_NATIVE && h->dt == SV_C64 && k >= 5 && g.c.empty()) {
-        // tensor-core path works on 6 targets; a 5-target block gains one identity qubit
+        // tensor-core path works on 6 targets; a 5-target block gains one identity
+        // qubit, the highest one not in the block (low qubits stay free, which keeps
+        // consecutive columns on adjacent amplitudes)
         std::vector<int> t6 = g.t;
         std::vector<double> m6;
         if (k == 5) {
             int extra = -1;
-            for (int q = 0; q < h->n && extra < 0; ++q)
+            for (int q = h->n - 1; q >= 0 && extra < 0; --q)
                 if (std::find(t6.begin(), t6.end(), q) == t6.end()) extra = q;
             if (extra < 0) return SV_ERR_INVALID_ARGUMENT;
             Gate g6;

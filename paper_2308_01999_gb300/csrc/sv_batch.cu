@@ -1,0 +1,362 @@
+// sv_batch.cu -- host side of the batched small-state engine (include/sv.h,
+// "Batched small state vectors"): compile many independent circuits into one
+// program and run it in one persistent launch (k_batch.cu).
+//
+// Per state: the gates are fused greedily into blocks of at most
+// `fusion_width` qubits (Sec. II-B, the same pass as sv_apply_fused), every
+// block goes through the exact structure analysis of sv_apply_matrix
+// (controls extracted; diagonal / generalized-permutation / dense), and the
+// resulting ops are grouped into stages of at most 14 local qubits with the
+// same commutation-aware greedy rule (an op may join any stage at or after the
+// last stage touching its qubits). Compilation is host-only; the program is
+// uploaded and run by sv_batch_launch.
+#include <algorithm>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sv_classify.h"
+#include "sv_fuse.h"
+#include "sv_internal.h"
+
+using cd = std::complex<double>;
+
+struct sv_batch_ctx {
+    cudaStream_t stream = nullptr;
+    int device = -1;
+    int num_sms = 0;
+    // compiled program (host)
+    std::vector<svk::BItem> items;
+    std::vector<svk::BStage> stages;
+    std::vector<svk::BOp> ops;
+    std::vector<float2> pool;
+    std::vector<svk::BStr> strs;
+    int n_out = 0;
+    uint64_t state_amps = 0;     // amplitudes the states need in d_states
+    bool compiled = false;
+    // device copy
+    char *dbuf = nullptr;
+    size_t dbuf_bytes = 0;
+    double *d_out = nullptr;
+    int *d_counter = nullptr;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+using svc::Gate;
+
+struct QOp {                     // an op in global qubit numbering
+    int kind;
+    std::vector<int> t, c, cv;   // targets (ascending for dense/perm), controls, values
+    std::vector<cd> data;        // dense: D*D; diag: D; perm: factors (D) then destinations (D, as numbers)
+    uint64_t qmask;
+};
+
+bool gate_ok(const sv_gate_t &g, int n) {
+    if (g.n_targets < 1 || g.n_targets > 4 || g.n_controls < 0 || g.n_controls > 8 || !g.matrix ||
+        g.n_targets + g.n_controls > std::min(n, svk::kBatchTileQubits))
+        return false;
+    uint64_t seen = 0;
+    for (int i = 0; i < g.n_targets + g.n_controls; ++i) {
+        const int q = i < g.n_targets ? g.targets[i] : g.controls[i - g.n_targets];
+        if (q < 0 || q >= n || ((seen >> q) & 1u)) return false;
+        seen |= 1ull << q;
+    }
+    for (int i = 0; i < g.n_controls; ++i)
+        if (g.control_values[i] != 0 && g.control_values[i] != 1) return false;
+    return true;
+}
+
+// exact structure analysis of one (fused) gate -> at most one op
+bool classify(Gate g, std::vector<QOp> &out) {
+    svc::simplify_controls(g);
+    const int k = (int)g.t.size();
+    QOp op;
+    op.c = g.c;
+    op.cv = g.cv;
+    if (k == 0) {
+        if (g.m[0] == cd(1)) return true;            // identity
+        op.kind = svk::BOP_DIAG;
+        op.data = {g.m[0]};
+    } else if (svc::is_diagonal(g)) {
+        op.kind = svk::BOP_DIAG;
+        op.t = g.t;
+        const int D = 1 << k;
+        for (int j = 0; j < D; ++j) op.data.push_back(g.m[j * D + j]);
+    } else {
+        svc::sort_targets(g);
+        op.t = g.t;
+        std::vector<int> perm;
+        std::vector<cd> d;
+        const int D = 1 << k;
+        if (k > 4) return false;
+        if (svc::as_permutation(g, perm, d)) {
+            // source member l = perm[j] goes to destination j with factor d[j]
+            op.kind = svk::BOP_PERM;
+            op.data.assign(2 * D, cd(0));
+            for (int j = 0; j < D; ++j) {
+                op.data[perm[j]] = d[j];
+                op.data[D + perm[j]] = cd((double)j, 0);
+            }
+        } else {
+            op.kind = svk::BOP_DENSE;
+            op.data = g.m;
+        }
+    }
+    op.qmask = 0;
+    for (int q : op.t) op.qmask |= 1ull << q;
+    for (int q : op.c) op.qmask |= 1ull << q;
+    out.push_back(std::move(op));
+    return true;
+}
+
+int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+// local position of global qubit q in a stage with local mask lmask
+uint8_t local_pos(uint64_t lmask, int q) { return (uint8_t)popc64(lmask & ((1ull << q) - 1ull)); }
+
+}  // namespace
+
+extern "C" {
+
+SV_API sv_status_t sv_batch_create(void *stream, sv_batch_t *out) {
+    if (!out) return SV_ERR_INVALID_ARGUMENT;
+    sv_batch_ctx *b = new (std::nothrow) sv_batch_ctx();
+    if (!b) return SV_ERR_ALLOC;
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    *out = b;
+    return SV_OK;
+}
+
+SV_API sv_status_t sv_batch_destroy(sv_batch_t b) {
+    if (!b) return SV_ERR_INVALID_ARGUMENT;
+    if (b->dbuf) {
+        cudaStreamSynchronize(b->stream);
+        cudaFree(b->dbuf);
+    }
+    delete b;
+    return SV_OK;
+}
+
+SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, int n_items, const sv_gate_t *gates,
+                                    int n_gates_total, const int *paulis, int fusion_width) {
+    if (!b || (!items && n_items > 0) || n_items < 0 || fusion_width < 1 || fusion_width > 4 ||
+        (n_gates_total > 0 && !gates) || n_gates_total < 0)
+        return SV_ERR_INVALID_ARGUMENT;
+    b->compiled = false;
+    b->items.clear();
+    b->stages.clear();
+    b->ops.clear();
+    b->pool.clear();
+    b->strs.clear();
+    b->n_out = 0;
+    b->state_amps = 0;
+    // largest states first: they take longest, so they start first
+    std::vector<int> order(n_items);
+    for (int i = 0; i < n_items; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return items[a].n_qubits > items[c].n_qubits; });
+    for (int oi : order) {
+        const sv_batch_item_t &it = items[oi];
+        const int n = it.n_qubits;
+        if (n < 1 || n > SV_BATCH_MAX_QUBITS || it.n_gates < 0 || it.gate_begin < 0 ||
+            it.gate_begin + it.n_gates > n_gates_total || it.n_strings < 0 || it.out_begin < 0 ||
+            (it.n_strings > 0 && (!paulis || it.pauli_begin < 0)))
+            return SV_ERR_INVALID_ARGUMENT;
+        for (int g = 0; g < it.n_gates; ++g)
+            if (!gate_ok(gates[it.gate_begin + g], n)) return SV_ERR_INVALID_ARGUMENT;
+        b->n_out = std::max(b->n_out, it.out_begin + it.n_strings);
+        b->state_amps = std::max<uint64_t>(b->state_amps, it.state_offset + (1ull << n));
+        // fusion, then structure analysis
+        std::vector<svf::Item> fused;
+        sv_status_t s = svf::fuse(gates + it.gate_begin, it.n_gates, n, fusion_width, fused);
+        if (s != SV_OK) return s;
+        std::vector<QOp> qops;
+        for (const svf::Item &f : fused) {
+            Gate g;
+            if (f.passthrough) {
+                const sv_gate_t &sg = gates[it.gate_begin + f.gate];
+                g.t.assign(sg.targets, sg.targets + sg.n_targets);
+                g.c.assign(sg.controls, sg.controls + sg.n_controls);
+                g.cv.assign(sg.control_values, sg.control_values + sg.n_controls);
+                const int D = 1 << sg.n_targets;
+                g.m.resize(D * D);
+                for (int i = 0; i < D * D; ++i) g.m[i] = cd(sg.matrix[2 * i], sg.matrix[2 * i + 1]);
+            } else {
+                g.t = f.qubits;
+                g.m = f.m;
+            }
+            if (!classify(g, qops)) return SV_ERR_NOT_SUPPORTED;
+        }
+        // stages of at most T local qubits
+        const int T = std::min(n, svk::kBatchTileQubits);
+        struct St { uint64_t q; std::vector<int> ops; };
+        std::vector<St> sts;
+        std::vector<int> last(n, -1);
+        for (int oi2 = 0; oi2 < (int)qops.size(); ++oi2) {
+            const uint64_t qm = qops[oi2].qmask;
+            int L = -1;
+            for (int q = 0; q < n; ++q)
+                if ((qm >> q) & 1u) L = std::max(L, last[q]);
+            int best = -1, best_growth = 1 << 30;
+            for (int j = std::max(L, 0); j < (int)sts.size(); ++j) {
+                const int growth = popc64(qm & ~sts[j].q);
+                if (popc64(sts[j].q | qm) <= T && growth < best_growth) {
+                    best = j;
+                    best_growth = growth;
+                }
+            }
+            if (best < 0) {
+                sts.push_back({0, {}});
+                best = (int)sts.size() - 1;
+            }
+            sts[best].q |= qm;
+            sts[best].ops.push_back(oi2);
+            for (int q = 0; q < n; ++q)
+                if ((qm >> q) & 1u) last[q] = best;
+        }
+        if (sts.empty()) sts.push_back({0, {}});
+        svk::BItem bi{};
+        bi.state_off = it.state_offset;
+        bi.n = n;
+        bi.T = T;
+        bi.stage_begin = (int)b->stages.size();
+        for (St &st : sts) {
+            // fill the local set with the lowest remaining qubits (contiguous tile rows)
+            uint64_t lm = st.q;
+            for (int q = 0; q < n && popc64(lm) < T; ++q) lm |= 1ull << q;
+            svk::BStage bs{};
+            bs.lmask = lm;
+            bs.op_begin = (int)b->ops.size();
+            for (int oidx : st.ops) {
+                const QOp &qo = qops[oidx];
+                svk::BOp op{};
+                op.kind = (uint8_t)qo.kind;
+                op.k = (uint8_t)qo.t.size();
+                for (size_t i = 0; i < qo.t.size(); ++i) op.t[i] = local_pos(lm, qo.t[i]);
+                std::vector<int> ins;
+                if (qo.kind != svk::BOP_DIAG)
+                    for (int q : qo.t) ins.push_back(local_pos(lm, q));
+                for (int q : qo.c) ins.push_back(local_pos(lm, q));
+                std::sort(ins.begin(), ins.end());
+                op.np = (uint8_t)ins.size();
+                for (size_t i = 0; i < ins.size(); ++i) op.p[i] = (uint8_t)ins[i];
+                op.cval = 0;
+                for (size_t i = 0; i < qo.c.size(); ++i)
+                    if (qo.cv[i]) op.cval |= 1u << local_pos(lm, qo.c[i]);
+                op.mat = (uint32_t)b->pool.size();
+                const int D = 1 << op.k;
+                for (size_t i = 0; i < qo.data.size(); ++i) {
+                    float2 v;
+                    if (qo.kind == svk::BOP_PERM && (int)i >= D) {
+                        const int dst = (int)qo.data[i].real();
+                        std::memcpy(&v.x, &dst, 4);
+                        v.y = 0.f;
+                    } else {
+                        v = make_float2((float)qo.data[i].real(), (float)qo.data[i].imag());
+                    }
+                    b->pool.push_back(v);
+                }
+                b->ops.push_back(op);
+            }
+            bs.op_end = (int)b->ops.size();
+            b->stages.push_back(bs);
+        }
+        bi.stage_end = (int)b->stages.size();
+        // Pauli strings: codes paulis[pauli_begin + s * n + q] act on qubit q
+        bi.str_begin = (int)b->strs.size();
+        bi.n_str = it.n_strings;
+        bi.out_begin = it.out_begin;
+        for (int s = 0; s < it.n_strings; ++s) {
+            uint64_t x = 0, z = 0;
+            int ny = 0;
+            for (int q = 0; q < n; ++q) {
+                const int p = paulis[(size_t)it.pauli_begin + (size_t)s * n + q];
+                if (p < 0 || p > 3) return SV_ERR_INVALID_ARGUMENT;
+                if (p == SV_PAULI_X || p == SV_PAULI_Y) x |= 1ull << q;
+                if (p == SV_PAULI_Z || p == SV_PAULI_Y) z |= 1ull << q;
+                ny += p == SV_PAULI_Y;
+            }
+            const int r = ny & 3;   // i^{nY}: +Re, -Im, -Re, +Im
+            b->strs.push_back({x, z, r & 1, (r == 1 || r == 2) ? -1.f : 1.f});
+        }
+        b->items.push_back(bi);
+    }
+    b->compiled = true;
+    return SV_OK;
+}
+
+SV_API sv_status_t sv_batch_info(sv_batch_t b, int *n_items, int *n_stages, int *n_ops, uint64_t *state_amps,
+                                 uint64_t *launches) {
+    if (!b) return SV_ERR_INVALID_ARGUMENT;
+    if (n_items) *n_items = (int)b->items.size();
+    if (n_stages) *n_stages = (int)b->stages.size();
+    if (n_ops) *n_ops = (int)b->ops.size();
+    if (state_amps) *state_amps = b->state_amps;
+    if (launches) *launches = b->launches;
+    return SV_OK;
+}
+
+SV_API sv_status_t sv_batch_launch(sv_batch_t b, sv_dtype_t dtype, void *d_states, int flags) {
+    if (!b || !b->compiled || !d_states || (reinterpret_cast<uintptr_t>(d_states) & 15u)) return SV_ERR_INVALID_ARGUMENT;
+    if (dtype != SV_C64) return SV_ERR_NOT_SUPPORTED;
+    if (b->items.empty()) return SV_OK;
+    if (b->device < 0) {
+        if (cudaGetDevice(&b->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+            return SV_ERR_CUDA;
+    }
+    auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t o_items = 0;
+    const size_t o_stages = align(o_items + b->items.size() * sizeof(svk::BItem));
+    const size_t o_ops = align(o_stages + b->stages.size() * sizeof(svk::BStage));
+    const size_t o_pool = align(o_ops + b->ops.size() * sizeof(svk::BOp));
+    const size_t o_strs = align(o_pool + b->pool.size() * sizeof(float2));
+    const size_t o_out = align(o_strs + b->strs.size() * sizeof(svk::BStr));
+    const size_t o_cnt = align(o_out + (size_t)b->n_out * sizeof(double));
+    const size_t total = o_cnt + 256;
+    if (total > b->dbuf_bytes) {
+        if (b->dbuf) {
+            cudaStreamSynchronize(b->stream);
+            cudaFree(b->dbuf);
+            b->dbuf = nullptr;
+            b->dbuf_bytes = 0;
+        }
+        if (cudaMalloc(reinterpret_cast<void **>(&b->dbuf), total) != cudaSuccess) {
+            cudaGetLastError();
+            return SV_ERR_ALLOC;
+        }
+        b->dbuf_bytes = total;
+    }
+    auto up = [&](size_t off, const void *src, size_t bytes) {
+        return bytes == 0 ? cudaSuccess
+                          : cudaMemcpyAsync(b->dbuf + off, src, bytes, cudaMemcpyHostToDevice, b->stream);
+    };
+    if (up(o_items, b->items.data(), b->items.size() * sizeof(svk::BItem)) != cudaSuccess ||
+        up(o_stages, b->stages.data(), b->stages.size() * sizeof(svk::BStage)) != cudaSuccess ||
+        up(o_ops, b->ops.data(), b->ops.size() * sizeof(svk::BOp)) != cudaSuccess ||
+        up(o_pool, b->pool.data(), b->pool.size() * sizeof(float2)) != cudaSuccess ||
+        up(o_strs, b->strs.data(), b->strs.size() * sizeof(svk::BStr)) != cudaSuccess)
+        return SV_ERR_CUDA;
+    b->d_out = reinterpret_cast<double *>(b->dbuf + o_out);
+    b->d_counter = reinterpret_cast<int *>(b->dbuf + o_cnt);
+    const svk::LaunchCtx L{b->stream, b->num_sms, &b->launches};
+    cudaError_t e = svk::launch_batch(
+        L, reinterpret_cast<float2 *>(d_states), reinterpret_cast<const svk::BItem *>(b->dbuf + o_items),
+        (int)b->items.size(), reinterpret_cast<const svk::BStage *>(b->dbuf + o_stages),
+        reinterpret_cast<const svk::BOp *>(b->dbuf + o_ops), reinterpret_cast<const float2 *>(b->dbuf + o_pool),
+        reinterpret_cast<const svk::BStr *>(b->dbuf + o_strs), b->d_out, b->d_counter, (flags & 1) ? 1 : 0);
+    return e == cudaSuccess ? SV_OK : SV_ERR_CUDA;
+}
+
+SV_API sv_status_t sv_batch_results(sv_batch_t b, double *out, int n_out) {
+    if (!b || !b->compiled || (!out && n_out > 0) || n_out < b->n_out) return SV_ERR_INVALID_ARGUMENT;
+    if (b->n_out == 0) return cudaStreamSynchronize(b->stream) == cudaSuccess ? SV_OK : SV_ERR_CUDA;
+    if (!b->d_out) return SV_ERR_INVALID_ARGUMENT;
+    if (cudaMemcpyAsync(out, b->d_out, sizeof(double) * b->n_out, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+        return SV_ERR_CUDA;
+    return cudaStreamSynchronize(b->stream) == cudaSuccess ? SV_OK : SV_ERR_CUDA;
+}
+
+}  // extern "C"

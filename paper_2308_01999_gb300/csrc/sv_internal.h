@@ -75,4 +75,47 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
                        sv_precision_t prec, void *d_a, int *d_err);
 bool tc6_supported(int n, const int *tpos);
 
+// ---- batched small states (k_batch.cu, sv_batch.cu) ----
+// One persistent launch advances many independent states. Each state's gates
+// are compiled into ops on local bit positions of a tile of 2^T amplitudes
+// (T = min(n, kBatchTileQubits)) and grouped into stages: a stage names T
+// "local" qubits (lmask) and its ops act on local qubits only, so one pass
+// over the state -- 2^(n-T) tiles, each gathered into shared memory once --
+// applies all of them.
+constexpr int kBatchTileQubits = 14;
+constexpr int kBatchThreads = 512;
+enum BatchOpKind { BOP_DENSE = 0, BOP_DIAG = 1, BOP_PERM = 2 };
+
+struct BItem {
+    uint64_t state_off;      // amplitude offset of the state
+    int n, T;                // qubits, tile qubits
+    int stage_begin, stage_end;
+    int str_begin, n_str;    // Pauli strings
+    int out_begin, pad;
+};
+
+struct BStage {
+    uint64_t lmask;          // the T local qubits
+    int op_begin, op_end;
+};
+
+struct BOp {
+    uint8_t kind, k, np, nt;  // kind, targets, inserted positions, (unused)
+    uint8_t t[4];             // local target positions (ascending for dense / perm)
+    uint8_t p[12];            // local inserted positions, ascending (targets + controls; controls only for diag)
+    uint32_t cval;            // local control bits that must be 1
+    uint32_t mat;             // offset into the matrix pool (float2 units)
+    uint32_t pad[2];
+};
+
+struct BStr {
+    uint64_t x, z;           // X|Y and Z|Y masks
+    int use_im;              // odd number of Y: take Im(w)
+    float sign;              // from i^{nY}
+};
+
+cudaError_t launch_batch(const LaunchCtx &L, float2 *states, const BItem *items, int n_items, const BStage *stages,
+                         const BOp *ops, const float2 *pool, const BStr *strs, double *out, int *counter,
+                         int keep_states);
+
 }  // namespace svk

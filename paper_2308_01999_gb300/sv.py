@@ -39,6 +39,8 @@ EXPORTED = [
     "sv_copy_from_host", "sv_copy_to_host", "sv_apply_matrix", "sv_apply_fused", "sv_fuse_plan",
     "sv_expectation_pauli", "sv_measure_probs", "sv_collapse", "sv_measure", "sv_norm2",
     "sv_check_device_status", "sv_launch_count", "sv_status_string", "sv_expectation_pauli_noalloc",
+    "sv_batch_create", "sv_batch_destroy", "sv_batch_compile", "sv_batch_info", "sv_batch_launch",
+    "sv_batch_results",
 ]
 
 
@@ -81,6 +83,11 @@ def lib():
             "sv_norm2": [_VP, _D], "sv_check_device_status": [_VP],
             "sv_launch_count": [_VP, C.POINTER(C.c_uint64)],
             "sv_expectation_pauli_noalloc": [C.c_int, C.c_int, _VP, _VP, _I, _I, C.c_int, C.c_int, _D],
+            "sv_batch_create": [_VP, C.POINTER(_VP)], "sv_batch_destroy": [_VP],
+            "sv_batch_compile": [_VP, _VP, C.c_int, _VP, C.c_int, _I, C.c_int],
+            "sv_batch_info": [_VP, _I, _I, _I, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
+            "sv_batch_launch": [_VP, C.c_int, _VP, C.c_int],
+            "sv_batch_results": [_VP, _D, C.c_int],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -355,3 +362,140 @@ class StateVector:
 
     def launches(self) -> int:
         return sv_launch_count(self.handle)
+
+
+# ---- batched small states ----
+
+SV_BATCH_KEEP_STATES = 1
+GATE_DTYPE = np.dtype([("n_targets", "<i4"), ("targets", "<i4", (SV_MAX_TARGETS,)), ("n_controls", "<i4"),
+                       ("controls", "<i4", (SV_MAX_CONTROLS,)), ("control_values", "<i4", (SV_MAX_CONTROLS,)),
+                       ("matrix", "<u8")])
+ITEM_DTYPE = np.dtype([("n_qubits", "<i4"), ("gate_begin", "<i4"), ("n_gates", "<i4"), ("pauli_begin", "<i4"),
+                       ("n_strings", "<i4"), ("out_begin", "<i4"), ("state_offset", "<u8")])
+
+
+def pack_gates(gates):
+    """sv_gate_t records for `gates` (a numpy structured array with the C layout)
+    and the complex128 buffer their matrix pointers point into (keep both alive)."""
+    assert C.sizeof(sv_gate_t) == GATE_DTYPE.itemsize
+    sizes = [g.matrix.size for g in gates]
+    buf = np.empty(max(1, sum(sizes)), dtype=np.complex128)
+    rec = np.zeros(len(gates), dtype=GATE_DTYPE)
+    base = buf.ctypes.data
+    off = 0
+    for i, g in enumerate(gates):
+        m = g.matrix.reshape(-1)
+        buf[off:off + m.size] = m
+        r = rec[i]
+        k = len(g.targets)
+        r["n_targets"] = k
+        r["targets"][:k] = g.targets
+        c = len(g.controls)
+        r["n_controls"] = c
+        if c:
+            r["controls"][:c] = g.controls
+            r["control_values"][:c] = g.control_values if g.control_values else (1,) * c
+        r["matrix"] = base + 16 * off
+        off += m.size
+    return rec, buf
+
+
+def sv_batch_create(stream_ptr: int = 0) -> int:
+    b = _VP()
+    _check(lib().sv_batch_create(_VP(stream_ptr), C.byref(b)), "sv_batch_create")
+    return b.value
+
+
+def sv_batch_destroy(b: int):
+    _check(lib().sv_batch_destroy(_VP(b)), "sv_batch_destroy")
+
+
+def sv_batch_compile(b: int, items: np.ndarray, gate_rec: np.ndarray, paulis: np.ndarray, fusion_width: int):
+    items = np.ascontiguousarray(items, dtype=ITEM_DTYPE)
+    gate_rec = np.ascontiguousarray(gate_rec, dtype=GATE_DTYPE)
+    paulis = np.ascontiguousarray(paulis, dtype=np.int32).reshape(-1)
+    _check(lib().sv_batch_compile(_VP(b), _VP(items.ctypes.data), int(items.size), _VP(gate_rec.ctypes.data),
+                                  int(gate_rec.size), paulis.ctypes.data_as(_I) if paulis.size else None,
+                                  int(fusion_width)), "sv_batch_compile")
+
+
+def sv_batch_info(b: int) -> dict:
+    ni, ns, no = C.c_int(), C.c_int(), C.c_int()
+    amps, launches = C.c_uint64(), C.c_uint64()
+    _check(lib().sv_batch_info(_VP(b), C.byref(ni), C.byref(ns), C.byref(no), C.byref(amps), C.byref(launches)),
+           "sv_batch_info")
+    return {"items": ni.value, "stages": ns.value, "ops": no.value, "state_amps": amps.value,
+            "launches": launches.value}
+
+
+def sv_batch_launch(b: int, d_states_ptr: int, keep_states: bool = False, dtype: int = SV_C64):
+    _check(lib().sv_batch_launch(_VP(b), int(dtype), _VP(d_states_ptr), SV_BATCH_KEEP_STATES if keep_states else 0),
+           "sv_batch_launch")
+
+
+def sv_batch_results(b: int, n_out: int) -> np.ndarray:
+    out = np.zeros(max(1, n_out), dtype=np.float64)
+    _check(lib().sv_batch_results(_VP(b), out.ctypes.data_as(_D), int(n_out)), "sv_batch_results")
+    return out[:n_out]
+
+
+class Batch:
+    """Many independent small circuits (from |0...0>) advanced in one launch.
+
+    states: list of (n_qubits, gates, paulis) with paulis an (S, n_qubits) int
+    array of Pauli codes (column q acts on qubit q). Results come back in input
+    order, S values per state."""
+
+    def __init__(self, stream=None):
+        self.stream = stream
+        ptr = stream.cuda_stream if stream is not None else 0
+        self.handle = sv_batch_create(ptr)
+        self._keep = None
+
+    def compile(self, states, fusion_width: int = 2):
+        items = np.zeros(len(states), dtype=ITEM_DTYPE)
+        all_gates, pls = [], []
+        g0 = p0 = o0 = 0
+        a0 = 0
+        for i, (n, gates, paulis) in enumerate(states):
+            paulis = np.asarray(paulis, dtype=np.int32).reshape(-1, n) if len(paulis) else np.zeros((0, n), np.int32)
+            items[i] = (n, g0, len(gates), p0, paulis.shape[0], o0, a0)
+            all_gates.extend(gates)
+            pls.append(paulis.reshape(-1))
+            g0 += len(gates)
+            p0 += paulis.size
+            o0 += paulis.shape[0]
+            a0 += 1 << n
+        rec, buf = pack_gates(all_gates)
+        pl = np.concatenate(pls) if pls else np.zeros(0, np.int32)
+        sv_batch_compile(self.handle, items, rec, pl, fusion_width)
+        self._keep = (items, rec, buf, pl)
+        self.n_out = o0
+        self.state_amps = a0
+        self.offsets = [(int(it["state_offset"]), int(it["n_qubits"]), int(it["out_begin"]), int(it["n_strings"]))
+                        for it in items]
+        return self.info()
+
+    def info(self):
+        return sv_batch_info(self.handle)
+
+    def launch(self, d_states, keep_states: bool = False):
+        """d_states: a complex64 CUDA tensor of at least `state_amps` elements."""
+        if d_states.numel() < self.state_amps:
+            raise ValueError("d_states is too small for this batch")
+        sv_batch_launch(self.handle, d_states.data_ptr(), keep_states)
+
+    def results(self):
+        flat = sv_batch_results(self.handle, self.n_out)
+        return [flat[o:o + s] for (_, _, o, s) in self.offsets]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sv_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,108 @@
+"""The batched small-state engine: host compilation (CPU) and GPU parity of
+many independent circuits run in one persistent launch against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2308_01999_gb300 import inputs as gen
+
+
+@pytest.fixture(scope="module")
+def svmod():
+    from paper_2308_01999_gb300 import _build
+    _build.build()
+    from paper_2308_01999_gb300 import sv
+    sv.lib()
+    return sv
+
+
+def _mixed_states(seed, sizes, strings=5):
+    rng = gen.rng_for(seed)
+    states = []
+    for i, n in enumerate(sizes):
+        if i % 3 == 0:
+            gates = gen.ansatz_circuit(n, 3, rng)
+        elif i % 3 == 1:
+            gates = gen.layered_random_circuit(n, 3, seed + i, ("cz", "cnot", "crz")) if n >= 2 else \
+                [gen.Gate((0,), gen.haar_su2(rng))]
+        else:
+            gates = []
+            for _ in range(12):
+                k = int(rng.integers(1, min(3, n) + 1))
+                c = int(rng.integers(0, min(2, n - k) + 1))
+                qs = [int(x) for x in rng.choice(n, k + c, replace=False)]
+                gates.append(gen.Gate(tuple(qs[:k]), gen.random_gate_dense(rng, k), tuple(qs[k:]),
+                                      tuple(int(v) for v in rng.integers(0, 2, size=c))))
+        paulis, _ = gen.random_pauli_strings(n, strings, rng)
+        states.append((n, gates, paulis))
+    return states
+
+
+def test_compile_on_host_only(svmod):
+    sv = svmod
+    b = sv.Batch()
+    states = _mixed_states(1, [3, 10, 14, 16, 18])
+    info = b.compile(states, fusion_width=2)
+    assert info["items"] == 5 and info["launches"] == 0
+    assert info["state_amps"] == sum(1 << n for n, _, _ in states)
+    # states of <= 14 qubits take one pass; larger ones need more than one
+    one = sv.Batch()
+    assert one.compile(states[:3], 3)["stages"] == 3
+    assert info["stages"] > 5
+    with pytest.raises(sv.SvError):
+        sv.Batch().compile([(3, [gen.Gate((3,), np.eye(2))], np.zeros((0, 3)))], 2)
+    with pytest.raises(sv.SvError):
+        sv.Batch().compile([(21, [], np.zeros((0, 21)))], 2)
+    with pytest.raises(sv.SvError):
+        sv.Batch().compile(states, 5)
+    b.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("width", [1, 2, 3, 4])
+def test_batch_matches_oracle(svmod, width):
+    import torch
+    sv = svmod
+    sizes = [1, 2, 5, 10, 12, 13, 14, 15, 16, 17, 18, 4, 11, 14, 16]
+    states = _mixed_states(10 + width, sizes)
+    b = sv.Batch(torch.cuda.current_stream())
+    b.compile(states, fusion_width=width)
+    buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
+    b.launch(buf, keep_states=True)
+    res = b.results()
+    host = buf.cpu().numpy()
+    for (n, gates, paulis), (off, _, _, _), got in zip(states, b.offsets, res):
+        ref = orc.run_circuit(gates, n)
+        amp = host[off:off + (1 << n)].astype(np.complex128)
+        err = np.max(np.abs(amp - ref))
+        assert err <= 1e-5, (n, width, err)
+        want = np.array([orc.expect_pauli(ref, p, list(range(n))).real for p in paulis])
+        assert np.all(np.abs(got - want) <= 1e-6 * np.maximum(1, np.abs(want))), (n, got, want)
+    b.close()
+
+
+@pytest.mark.gpu
+def test_batch_equals_single_state_path_and_repeats(svmod):
+    """The same circuits through sv_apply_matrix + sv_expectation_pauli one
+    state at a time; a second launch of the same program gives the same values."""
+    import torch
+    sv = svmod
+    states = _mixed_states(77, [10, 12, 14, 16, 20], strings=8)
+    b = sv.Batch(torch.cuda.current_stream())
+    b.compile(states, fusion_width=2)
+    buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
+    b.launch(buf)
+    first = [r.copy() for r in b.results()]
+    b.launch(buf)
+    second = b.results()
+    for a, c in zip(first, second):
+        assert np.array_equal(a, c)
+    for (n, gates, paulis), got in zip(states, first):
+        psi = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+        s = sv.StateVector(psi)
+        s.set_basis_state(0)
+        s.apply_circuit(gates)
+        want = s.expectation_pauli(paulis, np.tile(np.arange(n, dtype=np.int32), (paulis.shape[0], 1)))
+        assert np.all(np.abs(got - want) <= 1e-6 * np.maximum(1, np.abs(want))), (n, got, want)
+        s.close()
+    b.close()
