@@ -475,6 +475,18 @@ def run_fused(args):
                     rec["ms_by_lowest_target"] = {str(q): round(float(np.mean(v)), 2) for q, v in sorted(by_lo.items())}
                     rec["ms_by_highest_target"] = {str(q): round(float(np.mean(v)), 2) for q, v in sorted(by_hi.items())}
                 rec.update(errors())
+                # the same circuit as one sv_apply_fused call: host fusion, qubit
+                # relabelling (tensor-core precisions) and every block
+                s.set_basis_state(0)
+                torch.cuda.synchronize()
+                c0, c1 = event_pair()
+                h0 = time.perf_counter()
+                c0.record(stream)
+                s.apply_fused(gates, w, prec)
+                c1.record(stream)
+                torch.cuda.synchronize()
+                rec["one_call_s"] = round(c0.elapsed_time(c1) / 1e3, 3)
+                rec["one_call_wall_s"] = round(time.perf_counter() - h0, 3)
                 out[f"w{w}_{prec_name}"] = rec
                 print(json.dumps({f"w{w}_{prec_name}": rec}), file=sys.stderr, flush=True)
         s.close()
@@ -555,6 +567,60 @@ def run_batch(args):
     print(json.dumps(out))
 
 
+def run_serve(args):
+    """Serving trace: Poisson arrivals of random circuits (12..30 qubits, depth
+    10..60, the gate mix of the 28-qubit circuit, complex64), each returning
+    <Z_q> for all its qubits. The continuous-batching engine (admission by free
+    HBM, batched small states, one stream per large request, fused native
+    gates) against the plain engine (one request at a time, one launch per
+    gate) on the same trace; then both again at 0.7x the plain engine's
+    measured capacity, so that latency reflects service rather than backlog."""
+    import torch
+
+    from paper_2308_01999_gb300 import serving
+
+    torch.cuda.set_device(0)
+    ex = serving.GpuExecutor(fusion_width=4)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(0.8 * free, args.serve_budget_gb * (1 << 30)))
+    # warm-up of both paths (library load, first launches)
+    warm = serving.make_requests(gen.serving_trace(count=6, rate=1000.0, nmin=12, nmax=24, dmin=3, dmax=5, seed=99))
+    serving.ServingEngine(ex, budget).run(warm)
+    for r in warm[:2]:
+        ex.run_plain(r)
+    torch.cuda.synchronize()
+
+    def one(rate, count, seed):
+        trace = gen.serving_trace(count=count, rate=rate, seed=seed)
+        eng = serving.ServingEngine(ex, budget, small_max_qubits=20, large_workers=4)
+        mix = eng.run(serving.make_requests(trace))
+        occ = eng.occupancy
+        tw = 0.0
+        for (t_a, b_a), (t_b, _) in zip(occ, occ[1:]):
+            tw += b_a * (t_b - t_a)
+        span = occ[-1][0] - occ[0][0] if len(occ) > 1 else 1.0
+        plain = serving.serial_engine(ex.run_plain, serving.make_requests(trace))
+        diffs = [float(np.max(np.abs(a.result - b.result))) for a, b in zip(mix, plain)
+                 if a.result is not None and b.result is not None]
+        service = [r.t_done - r.t_admit for r in plain if r.error is None]
+        return {"requests": count, "rate_per_s": round(rate, 3),
+                "served": {k: round(v, 4) for k, v in serving.latency_stats(mix).items()},
+                "plain": {k: round(v, 4) for k, v in serving.latency_stats(plain).items()},
+                "hbm_peak_gib": round(eng.peak_bytes / (1 << 30), 2),
+                "hbm_mean_gib": round(tw / span / (1 << 30), 2),
+                "max_abs_diff_vs_plain": max(diffs) if diffs else None,
+                "plain_capacity_per_s": round(len(service) / sum(service), 3) if service else None}
+
+    out = {"workload": "serving trace, Poisson arrivals, qubits 12..30, depth 10..60, complex64, <Z_q> for all q",
+           "hbm_budget_gib": round(budget / (1 << 30), 1)}
+    hot = one(args.serve_rate, args.serve_requests, 4)
+    out["at_offered_rate"] = hot
+    print(json.dumps({"at_offered_rate": hot}), file=sys.stderr, flush=True)
+    cap = hot["plain_capacity_per_s"] or 1.0
+    out["at_0.7x_plain_capacity"] = one(0.7 * cap, args.serve_low_requests, 5)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -564,13 +630,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--qubits", type=int, default=28,
                     help="state size; 28 is the benchmark workload, smaller sizes are for profiling captures")
-    ap.add_argument("--workload", choices=("circuit28", "fused32", "batch"), default="circuit28",
+    ap.add_argument("--workload", choices=("circuit28", "fused32", "batch", "serve"), default="circuit28",
                     help="fused32: the 32-qubit fused brick-wall study (tensor cores, errors vs complex128)")
     ap.add_argument("--fused-qubits", type=int, default=32)
     ap.add_argument("--no-ref", action="store_true", help="fused32 without the complex128 reference run")
     ap.add_argument("--widths", default="5,6", help="fused32: fusion widths")
     ap.add_argument("--batch-states", type=int, default=4096, help="batch: number of states")
     ap.add_argument("--plain-sample", type=int, default=256, help="batch: states run through the plain engine")
+    ap.add_argument("--serve-requests", type=int, default=120, help="serve: requests of the offered-rate trace")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="serve: offered arrival rate (1/s)")
+    ap.add_argument("--serve-low-requests", type=int, default=40, help="serve: requests of the 0.7x-capacity trace")
+    ap.add_argument("--serve-budget-gb", type=float, default=200.0, help="serve: HBM budget for resident states")
     ap.add_argument("--precs", default="tf32,bf16,native", help="fused32: precisions")
     args = ap.parse_args()
     global N_QUBITS
@@ -581,6 +651,8 @@ def main():
         run_fused(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

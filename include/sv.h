@@ -137,6 +137,16 @@ SV_API sv_status_t sv_apply_matrix(sv_handle_t h, const int *targets, int n_targ
 SV_API sv_status_t sv_apply_fused(sv_handle_t h, const sv_gate_t *gates, int n_gates,
                            int max_fused_qubits, sv_precision_t prec, int *n_fused_out);
 
+/* Index-bit swap (Table I, "Index bit swap", single-GPU version; Sec. II-C,
+ * qubit reordering): for each of the n_pairs disjoint pairs
+ * (bit_pairs[2k], bit_pairs[2k+1]) exchange those two bits of every amplitude
+ * index, i.e. psi'[swap(i)] = psi[i]. This relabels the paired qubits (qubit a
+ * of the new state is qubit b of the old one). In place, one pass over the
+ * amplitudes whose paired bits differ. Asynchronous. Errors: INVALID_ARGUMENT
+ * for a bit outside [0, n), a bit used twice, a pair of equal bits, or
+ * n_pairs outside 1..18. */
+SV_API sv_status_t sv_swap_index_bits(sv_handle_t h, const int *bit_pairs, int n_pairs);
+
 /* Host-only view of the fusion pass, for inspection and tests (no GPU needed).
  * Writes at most max_blocks blocks: block b acts on block_k[b] qubits
  * block_targets[6*b .. 6*b+k-1] (bit j of its matrix index is target j) with
@@ -182,6 +192,22 @@ SV_API sv_status_t sv_expectation_pauli(sv_handle_t h, const int *paulis, const 
 SV_API sv_status_t sv_expectation_pauli_noalloc(int n_qubits, sv_dtype_t dtype, const void *d_state, void *stream,
                                                 const int *paulis, const int *sites, int n_sites, int n_strings,
                                                 double *out);
+
+/* Pauli rotation (Table I, "Pauli rotation"): psi <- exp(i theta P) psi =
+ * cos(theta) psi + i sin(theta) P psi, P = prod_i paulis[i] on qubit sites[i]
+ * (codes as sv_expectation_pauli). In place, one pass over the state.
+ * Asynchronous. Errors: INVALID_ARGUMENT for a bad code or site, a repeated
+ * site, a non-finite theta. */
+SV_API sv_status_t sv_apply_pauli_rotation(sv_handle_t h, double theta, const int *paulis, const int *sites,
+                                           int n_sites);
+
+/* Sampler (Table I, "Sampler"): measurement outcomes of all qubits without
+ * collapsing the state. For each randnums[t] in [0, 1), out[t] is the basis
+ * index i at which the cumulative probability sum_{k<=i} |psi_k|^2 first
+ * exceeds randnums[t] * <psi|psi> (probabilities summed in FP64). out is host
+ * memory of n_samples int64. Synchronises the stream. Errors:
+ * INVALID_ARGUMENT for a random number outside [0, 1) or NULL pointers. */
+SV_API sv_status_t sv_sample(sv_handle_t h, const double *randnums, int n_samples, int64_t *out);
 
 /* Probabilities of a measurement in the Z-product basis of `qubits` (Table I,
  * "Measurement"): p_even/p_odd = sum of |psi_i|^2 over basis states whose

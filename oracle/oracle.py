@@ -36,6 +36,10 @@ def lib():
         L.orc_collapse.restype = C.c_int
         L.orc_norm2.argtypes = [_D, C.c_int]
         L.orc_norm2.restype = C.c_double
+        L.orc_pauli_rotation.argtypes = [_D, C.c_int, _I, _I, C.c_int, C.c_double]
+        L.orc_pauli_rotation.restype = C.c_int
+        L.orc_sample.argtypes = [_D, C.c_int, _D, C.c_int, C.POINTER(C.c_int64)]
+        L.orc_sample.restype = C.c_int
         _lib = L
     return _lib
 
@@ -139,3 +143,26 @@ def measure(psi: np.ndarray, qubits, randnum: float, collapse: bool) -> int:
 
 def norm2(psi: np.ndarray) -> float:
     return float(lib().orc_norm2(_dptr(psi), _nqubits(psi)))
+
+
+def pauli_rotation(psi: np.ndarray, paulis, sites, theta: float) -> np.ndarray:
+    """psi <- exp(i theta P) psi in place."""
+    n = _nqubits(psi)
+    p, pp = _ints(paulis)
+    s, sp = _ints(sites)
+    rc = lib().orc_pauli_rotation(_dptr(psi), n, pp, sp, int(p.size), float(theta))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the rotation (code {rc})")
+    return psi
+
+
+def sample(psi: np.ndarray, randnums) -> np.ndarray:
+    """Basis indices drawn by inverting the cumulative probabilities at randnums."""
+    n = _nqubits(psi)
+    r = np.ascontiguousarray(np.asarray(randnums, dtype=np.float64))
+    out = np.zeros(r.size, dtype=np.int64)
+    rc = lib().orc_sample(_dptr(psi), n, r.ctypes.data_as(_D), int(r.size),
+                          out.ctypes.data_as(C.POINTER(C.c_int64)))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the sampling (code {rc})")
+    return out

@@ -19,7 +19,12 @@
  *                    a measurement in the Z-product basis (Table I, "Measurement");
  *   orc_collapse     collapse onto one parity outcome and renormalise
  *                    (Table I: probability and collapse are separate);
- *   orc_norm2        sum of |psi_i|^2.
+ *   orc_norm2        sum of |psi_i|^2;
+ *   orc_pauli_rotation  psi <- exp(i theta P) psi = cos(theta) psi + i sin(theta) P psi
+ *                    (Table I, "Pauli rotation"), P applied site by site;
+ *   orc_sample       measurement outcomes without collapse (Table I, "Sampler"):
+ *                    for each r in [0, 1) the basis index i with
+ *                    cum(i-1) <= r * cum(N-1) < cum(i), cum(i) = sum_{k<=i} |psi_k|^2.
  *
  * Conventions where the paper is silent: the row/column index bit j of a gate
  * matrix belongs to targets[j]; matrices are row-major; a control holds when
@@ -210,4 +215,63 @@ double orc_norm2(const double *psi_ri, int n)
         acc += a * a;
     }
     return acc;
+}
+
+/* psi <- cos(theta) psi + i sin(theta) P psi, P = prod_s paulis[s] on qubit sites[s] */
+int orc_pauli_rotation(double *psi_ri, int n, const int *paulis, const int *sites, int n_sites, double theta)
+{
+    if (n < 1 || n > 40 || n_sites < 0) return ORC_BAD_ARG;
+    uint64_t seen = 0;
+    for (int s = 0; s < n_sites; ++s) {
+        if (sites[s] < 0 || sites[s] >= n || paulis[s] < 0 || paulis[s] > 3) return ORC_BAD_ARG;
+        if ((seen >> sites[s]) & 1u) return ORC_BAD_ARG;
+        seen |= 1ull << sites[s];
+    }
+    const uint64_t N = 1ull << n;
+    zc *psi = (zc *)psi_ri;
+    zc *phi = (zc *)malloc(N * sizeof(zc));
+    if (!phi) return ORC_NO_MEM;
+    memcpy(phi, psi, N * sizeof(zc));
+    for (int s = 0; s < n_sites; ++s) {
+        if (paulis[s] == 0) continue;
+        zc m[4];
+        pauli_matrix(paulis[s], m);
+        int tq = sites[s];
+        orc_apply((double *)phi, n, &tq, 1, NULL, NULL, 0, (const double *)m);
+    }
+    const double c = cos(theta), sn = sin(theta);
+    for (uint64_t i = 0; i < N; ++i) psi[i] = c * psi[i] + I * sn * phi[i];
+    free(phi);
+    return ORC_OK;
+}
+
+/* out[t] = smallest i with r_t * cum(N-1) < cum(i) */
+int orc_sample(const double *psi_ri, int n, const double *randnums, int n_samples, int64_t *out)
+{
+    if (n < 1 || n > 40 || n_samples < 0) return ORC_BAD_ARG;
+    const uint64_t N = 1ull << n;
+    const zc *psi = (const zc *)psi_ri;
+    double *cum = (double *)malloc(N * sizeof(double));
+    if (!cum) return ORC_NO_MEM;
+    double acc = 0.0;
+    for (uint64_t i = 0; i < N; ++i) {
+        double a = cabs(psi[i]);
+        acc += a * a;
+        cum[i] = acc;
+    }
+    for (int t = 0; t < n_samples; ++t) {
+        if (!(randnums[t] >= 0.0 && randnums[t] < 1.0)) {
+            free(cum);
+            return ORC_BAD_ARG;
+        }
+        const double target = randnums[t] * acc;
+        uint64_t lo = 0, hi = N - 1;          /* first index with cum > target */
+        while (lo < hi) {
+            uint64_t mid = lo + (hi - lo) / 2;
+            if (cum[mid] > target) hi = mid; else lo = mid + 1;
+        }
+        out[t] = (int64_t)lo;
+    }
+    free(cum);
+    return ORC_OK;
 }

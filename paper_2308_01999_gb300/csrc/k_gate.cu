@@ -20,6 +20,7 @@
 //          control on bit 0: 8 bytes).
 // Within a warp, consecutive threads take consecutive units, so for every member
 // the warp reads one contiguous run (coalesced), also for high target qubits.
+#include <cmath>
 #include <vector>
 
 #include "sv_internal.h"
@@ -463,6 +464,180 @@ cudaError_t perm_any(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, co
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// index-bit swap (Table I, "Index bit swap"): exchange bits a_k <-> b_k of
+// every index for disjoint pairs, i.e. relabel qubits. The map is an
+// involution, so each pair of amplitudes is swapped once, by the thread of the
+// smaller index; amplitudes whose swapped bits agree stay.
+// ---------------------------------------------------------------------------
+struct SwapP {
+    int np;
+    int a[18], b[18];
+};
+
+__device__ __forceinline__ uint64_t swap_bits(uint64_t i, const SwapP &P) {
+#pragma unroll 1
+    for (int k = 0; k < P.np; ++k) {
+        const uint64_t d = ((i >> P.a[k]) ^ (i >> P.b[k])) & 1u;
+        i ^= (d << P.a[k]) | (d << P.b[k]);
+    }
+    return i;
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kThreads) k_swap(typename CT<R>::T *__restrict__ sv, uint64_t n_units, SwapP P) {
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    for (uint64_t u = (uint64_t)blockIdx.x * kThreads + threadIdx.x; u < n_units; u += stride) {
+        if constexpr (MODE == PAIR) {
+            const uint64_t i = u << 1, j = swap_bits(i, P);     // bit 0 is not swapped: i+1 -> j+1
+            if (j <= i) continue;
+            float2 *p = reinterpret_cast<float2 *>(sv);
+            const float4 x = ld16(p + i), y = ld16(p + j);
+            st16(p + i, y);
+            st16(p + j, x);
+        } else {
+            const uint64_t i = u, j = swap_bits(i, P);
+            if (j <= i) continue;
+            const typename CT<R>::T x = sv[i], y = sv[j];
+            sv[i] = y;
+            sv[j] = x;
+        }
+    }
+}
+
+template <typename R>
+cudaError_t swap_t(const LaunchCtx &L, void *sv, int n, const int *a, const int *b, int np) {
+    using C = typename CT<R>::T;
+    SwapP P{};
+    P.np = np;
+    bool bit0 = false;
+    for (int k = 0; k < np; ++k) {
+        P.a[k] = a[k];
+        P.b[k] = b[k];
+        bit0 |= a[k] == 0 || b[k] == 0;
+    }
+    uint64_t units = 1ull << n;
+    const bool pair = sizeof(R) == 4 && !bit0 && n >= 1;
+    if (pair) units >>= 1;
+    uint64_t grid = (units + kThreads - 1) / kThreads;
+    const uint64_t cap = (uint64_t)L.num_sms * 16;
+    if (grid > cap) grid = cap;
+    if (grid == 0) grid = 1;
+    if constexpr (sizeof(R) == 4) {
+        if (pair) {
+            k_swap<R, PAIR><<<(unsigned)grid, kThreads, 0, L.stream>>>(reinterpret_cast<C *>(sv), units, P);
+            ++*L.launches;
+            return cudaGetLastError();
+        }
+    }
+    k_swap<R, SCALAR><<<(unsigned)grid, kThreads, 0, L.stream>>>(reinterpret_cast<C *>(sv), units, P);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Pauli rotation (Table I, "Pauli rotation"): psi <- exp(i theta P) psi
+// = cos(theta) psi + i sin(theta) P psi, with P|k> = i^{nY} (-1)^{popcount(k & z)} |k ^ x>.
+// Output amplitude j takes its P-term from source k = j ^ x; unit pairs
+// (u, u ^ x) are read once and written once, as in the expectation kernel.
+// ---------------------------------------------------------------------------
+template <typename R> struct RotP {
+    uint64_t x, z;
+    int ny;
+    R c, s;
+};
+
+template <typename C>
+__device__ __forceinline__ C rot90(const C &a, int m) {   // a * i^m
+    C r;
+    r.x = (m == 0) ? a.x : (m == 1) ? -a.y : (m == 2) ? -a.x : a.y;
+    r.y = (m == 0) ? a.y : (m == 1) ? a.x : (m == 2) ? -a.y : -a.x;
+    return r;
+}
+
+template <typename R, typename C>
+__device__ __forceinline__ C rot_out(const C &self, const C &src, uint64_t k, const RotP<R> &P) {
+    const int m = (P.ny + 1 + 2 * (int)(__popcll(k & P.z) & 1)) & 3;
+    const C t = rot90(src, m);
+    C o;
+    o.x = fmac(P.c, self.x, P.s * t.x);
+    o.y = fmac(P.c, self.y, P.s * t.y);
+    return o;
+}
+
+template <typename R, int V>
+__global__ void __launch_bounds__(kThreads)
+k_pauli_rot(typename CT<R>::T *__restrict__ sv, uint64_t n_work, int pair_bit, uint64_t xu, unsigned xl, RotP<R> P) {
+    using C = typename CT<R>::T;
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    for (uint64_t w = (uint64_t)blockIdx.x * kThreads + threadIdx.x; w < n_work; w += stride) {
+        uint64_t ua = w;
+        if (pair_bit >= 0) {
+            const uint64_t lo = w & ((1ull << pair_bit) - 1ull);
+            ua = ((w ^ lo) << 1) | lo;
+        }
+        const uint64_t ub = ua ^ xu;
+        C A[V], B[V], NA[V], NB[V];
+        if constexpr (V == 2) {
+            const float4 f = ld16(reinterpret_cast<const float2 *>(sv) + 2 * ua);
+            A[0] = C{f.x, f.y};
+            A[V - 1] = C{f.z, f.w};
+            if (pair_bit >= 0) {
+                const float4 g = ld16(reinterpret_cast<const float2 *>(sv) + 2 * ub);
+                B[0] = C{g.x, g.y};
+                B[V - 1] = C{g.z, g.w};
+            }
+        } else {
+            A[0] = sv[ua];
+            if (pair_bit >= 0) B[0] = sv[ub];
+        }
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const uint64_t ja = ua * V + e;
+            if (pair_bit < 0) {
+                NA[e] = rot_out(A[e], xl ? A[V - 1 - e] : A[e], ja ^ P.x, P);
+            } else {
+                NA[e] = rot_out(A[e], xl ? B[V - 1 - e] : B[e], ja ^ P.x, P);
+                NB[e] = rot_out(B[e], xl ? A[V - 1 - e] : A[e], (ub * V + e) ^ P.x, P);
+            }
+        }
+        if constexpr (V == 2) {
+            st16(reinterpret_cast<float2 *>(sv) + 2 * ua, make_float4(NA[0].x, NA[0].y, NA[V - 1].x, NA[V - 1].y));
+            if (pair_bit >= 0)
+                st16(reinterpret_cast<float2 *>(sv) + 2 * ub, make_float4(NB[0].x, NB[0].y, NB[V - 1].x, NB[V - 1].y));
+        } else {
+            sv[ua] = NA[0];
+            if (pair_bit >= 0) sv[ub] = NB[0];
+        }
+    }
+}
+
+template <typename R>
+cudaError_t pauli_rot_t(const LaunchCtx &L, void *sv, int n, uint64_t x, uint64_t z, int ny, double theta) {
+    using C = typename CT<R>::T;
+    constexpr int V = sizeof(R) == 4 ? 2 : 1;
+    const int vb = V == 2 ? 1 : 0;
+    if (n < 1) return cudaErrorInvalidValue;
+    RotP<R> P{x, z, ny, (R)cos(theta), (R)sin(theta)};
+    const uint64_t n_units = (1ull << n) >> vb;
+    const unsigned xl = (unsigned)(x & (uint64_t)(V - 1));
+    const uint64_t xu = x >> vb;
+    int pair_bit = -1;
+    uint64_t n_work = n_units;
+    if (xu != 0) {
+        pair_bit = __builtin_ctzll(xu);
+        n_work = n_units / 2;
+    }
+    uint64_t grid = (n_work + kThreads - 1) / kThreads;
+    const uint64_t cap = (uint64_t)L.num_sms * 16;
+    if (grid > cap) grid = cap;
+    if (grid == 0) grid = 1;
+    k_pauli_rot<R, V><<<(unsigned)grid, kThreads, 0, L.stream>>>(reinterpret_cast<C *>(sv), n_work, pair_bit, xu, xl, P);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_dense(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, const GroupGeom &G, const int *tpos,
@@ -481,6 +656,16 @@ cudaError_t launch_perm(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, cons
                         int k, const int *perm, const double *d) {
     return dt == SV_C64 ? perm_any<float>(L, sv, n, G, tpos, k, perm, d)
                         : perm_any<double>(L, sv, n, G, tpos, k, perm, d);
+}
+
+cudaError_t launch_swap(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, const int *a, const int *b, int np) {
+    if (np < 1 || np > 18) return cudaErrorInvalidValue;
+    return dt == SV_C64 ? swap_t<float>(L, sv, n, a, b, np) : swap_t<double>(L, sv, n, a, b, np);
+}
+
+cudaError_t launch_pauli_rotation(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t x, uint64_t z, int ny,
+                                  double theta) {
+    return dt == SV_C64 ? pauli_rot_t<float>(L, sv, n, x, z, ny, theta) : pauli_rot_t<double>(L, sv, n, x, z, ny, theta);
 }
 
 }  // namespace svk

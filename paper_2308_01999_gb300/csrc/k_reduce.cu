@@ -286,6 +286,142 @@ cudaError_t collapse_t(const LaunchCtx &L, void *sv, int n, uint64_t mask, int p
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Sampler (Table I, "Sampler"): measurement outcomes without collapse. The
+// state is cut into segments of 2^seg_log amplitudes; their probabilities are
+// summed (FP32 runs of 16 terms, FP64 beyond, fixed order), the segment sums
+// are scanned into a cumulative distribution by one block in a fixed order,
+// and each sample -- one warp -- binary-searches the segment and scans it
+// with warp prefix sums for the first index whose cumulative probability
+// exceeds r * total.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_seg_sums(const typename CT<R>::T *__restrict__ sv, int seg_log, uint64_t n_seg, double *__restrict__ seg) {
+    __shared__ double red[kThreads / 32];
+    const uint64_t S = 1ull << seg_log;
+    for (uint64_t g = blockIdx.x; g < n_seg; g += gridDim.x) {
+        double acc = 0.0;
+        R run = R(0);
+        int cnt = 0;
+        for (uint64_t i = threadIdx.x; i < S; i += kThreads) {
+            const typename CT<R>::T a = sv[g * S + i];
+            run += a.x * a.x + a.y * a.y;
+            if (++cnt == 16) {
+                acc += (double)run;
+                run = R(0);
+                cnt = 0;
+            }
+        }
+        acc += (double)run;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+            seg[g] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// inclusive scan of seg[0 .. n) in place, one block of 1024 threads, fixed order
+__global__ void __launch_bounds__(1024) k_scan(double *__restrict__ seg, uint64_t n) {
+    __shared__ double part[1024];
+    const uint64_t per = (n + 1023) / 1024;
+    const uint64_t b = threadIdx.x * per, e = (b + per < n) ? b + per : n;
+    double run = 0.0;
+    for (uint64_t i = b; i < e; ++i) {
+        run += seg[i];
+        seg[i] = run;
+    }
+    part[threadIdx.x] = run;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 1024; ++i) {
+            const double v = part[i];
+            part[i] = t;
+            t += v;
+        }
+    }
+    __syncthreads();
+    const double off = part[threadIdx.x];
+    for (uint64_t i = b; i < e; ++i) seg[i] += off;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_sample(const typename CT<R>::T *__restrict__ sv, int seg_log, uint64_t n_seg, const double *__restrict__ seg,
+         const double *__restrict__ rands, int n_samples, long long *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int sidx = (int)((blockIdx.x * (uint64_t)kThreads + threadIdx.x) >> 5);
+    if (sidx >= n_samples) return;
+    const double total = seg[n_seg - 1];
+    const double target = rands[sidx] * total;
+    uint64_t lo = 0, hi = n_seg - 1;            // first segment with cum > target
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (seg[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    const double before = lo > 0 ? seg[lo - 1] : 0.0;
+    const double want = target - before;
+    const uint64_t S = 1ull << seg_log, base = lo * S;
+    double running = 0.0;
+    long long last_nz = (long long)base;
+    for (uint64_t c = 0; c < S; c += 32) {
+        const uint64_t i = base + c + lane;
+        double p = 0.0;
+        if (c + lane < S) {
+            const typename CT<R>::T a = sv[i];
+            p = (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+        }
+        double inc = p;                         // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, running + inc > want && p > 0.0);
+        if (hit) {
+            if (lane == 0) out[sidx] = (long long)(base + c + (__ffs(hit) - 1));
+            return;
+        }
+        const unsigned nz = __ballot_sync(0xffffffffu, p > 0.0);
+        if (nz) last_nz = (long long)(base + c + (31 - __clz(nz)));
+        running += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    // rounding left the target past the segment's own sum: its last nonzero amplitude
+    if (lane == 0) out[sidx] = last_nz;
+}
+
+template <typename R>
+cudaError_t sample_t(const LaunchCtx &L, const void *sv, int n, const double *d_r, int ns, double *d_seg,
+                     long long *d_out) {
+    using C = typename CT<R>::T;
+    int seg_log = n - 20 > 12 ? n - 20 : 12;
+    if (seg_log > n) seg_log = n;
+    const uint64_t n_seg = 1ull << (n - seg_log);
+    uint64_t grid = n_seg;
+    const uint64_t cap = (uint64_t)L.num_sms * 8;
+    if (grid > cap) grid = cap;
+    k_seg_sums<R><<<(unsigned)grid, kThreads, 0, L.stream>>>(reinterpret_cast<const C *>(sv), seg_log, n_seg, d_seg);
+    ++*L.launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_scan<<<1, 1024, 0, L.stream>>>(d_seg, n_seg);
+    ++*L.launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t blocks = ((uint64_t)ns * 32 + kThreads - 1) / kThreads;
+    k_sample<R><<<(unsigned)blocks, kThreads, 0, L.stream>>>(reinterpret_cast<const C *>(sv), seg_log, n_seg, d_seg,
+                                                             d_r, ns, d_out);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_pauli(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int n, const PauliPass &P,
@@ -307,6 +443,13 @@ cudaError_t launch_collapse(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, 
     if (n < 1) return cudaErrorInvalidValue;
     return dt == SV_C64 ? collapse_t<float>(L, sv, n, mask, parity, scale)
                         : collapse_t<double>(L, sv, n, mask, parity, scale);
+}
+
+cudaError_t launch_sample(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int n, const double *d_r, int n_samples,
+                          double *d_seg, long long *d_out) {
+    if (n < 1 || n_samples < 1) return cudaErrorInvalidValue;
+    return dt == SV_C64 ? sample_t<float>(L, sv, n, d_r, n_samples, d_seg, d_out)
+                        : sample_t<double>(L, sv, n, d_r, n_samples, d_seg, d_out);
 }
 
 cudaError_t launch_set_basis(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t index) {

@@ -15,9 +15,10 @@
 // three MMAs into one FP32 accumulator).
 //
 // Kernel structure (one persistent CTA per SM, 544 threads):
-//   warps 0-7   producers: gather a tile of 128 columns x 64 members from HBM
-//               (8-byte loads, consecutive lanes on consecutive columns), round
-//               or split, and store it to shared memory in the canonical K-major
+//   warps 0-7   producers: read a tile of 128 columns x 64 members from HBM in
+//               address order (16-byte loads, each warp load one contiguous
+//               512-byte run, whatever the target positions), round or split,
+//               and scatter it to shared memory in the canonical K-major
 //               128-byte-swizzled operand layout; two tile buffers;
 //   warp 16     MMA issuer: one thread issues tcgen05.mma (M = N = 128) into one
 //               of two TMEM accumulators and commits to mbarriers;
@@ -60,6 +61,10 @@ enum Prec { TF32 = 1, BF16 = 2 };
 struct TcSmem {
     unsigned long long full[2], empty[2], acc_full[2], acc_empty[2], done;
     uint64_t pd[kNT];   // column offset i in a tile -> amplitude offset (bits deposited around the targets)
+    // A tile's 8192 amplitudes in address order: index a (13 bits) deposited into
+    // the 13 tile bit positions (the 6 targets and the 7 lowest other bits).
+    uint64_t adr_lo[128], adr_hi[64];   // a's bits 0..6 / 7..12 -> amplitude offset
+    uint16_t ij_lo[128], ij_hi[64];     // the same bits -> column i | member j << 7
     unsigned tmem_base;
     int abort;
 };
@@ -227,6 +232,30 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
     }
     // A tile starts at a multiple of kNT columns, so col_base(t*kNT + i) = col_base(t*kNT) | pd[i]
     if (threadIdx.x < kNT) S.pd[threadIdx.x] = col_base((uint64_t)threadIdx.x, G);
+    if (threadIdx.x >= kNT && threadIdx.x < kNT + 192) {
+        // tile bit b (0..12) in ascending position: either target tj (member bit tj)
+        // or the k-th lowest non-target (column bit k); positions >= n only occur
+        // for states under 13 qubits and land in columns >= n_cols (never loaded)
+        const int e = threadIdx.x - kNT;
+        const bool hi = e >= 128;
+        const int v = hi ? e - 128 : e;
+        uint64_t adr = 0;
+        uint32_t ij = 0;
+        int b = 0, tj = 0, k = 0;
+        for (int p = 0; b < 13; ++p) {
+            const bool is_t = tj < 6 && G.pos[tj] == p;
+            if (!is_t && k >= 7) continue;
+            const int vb = hi ? b - 7 : b;
+            if (vb >= 0 && vb < (hi ? 6 : 7) && ((v >> vb) & 1)) {
+                adr |= 1ull << p;
+                ij |= is_t ? (1u << (7 + tj)) : (1u << k);
+            }
+            if (is_t) ++tj; else ++k;
+            ++b;
+        }
+        if (hi) { S.adr_hi[v] = adr; S.ij_hi[v] = (uint16_t)ij; }
+        else { S.adr_lo[v] = adr; S.ij_lo[v] = (uint16_t)ij; }
+    }
     // A image -> shared memory (plain copy; the host built the swizzled layout)
     for (int i = threadIdx.x; i < kAImg / 16; i += kThreadsTC) reinterpret_cast<uint4 *>(sA)[i] = a_img[i];
     fence_proxy_async();
@@ -244,45 +273,96 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
 
     if (warp < kProdWarps) {
         // ---------------- producers ----------------
-        const int n = threadIdx.x & (kNT - 1);          // column within the tile
-        const int qhalf = threadIdx.x >> 7;             // member quads 8*qhalf .. 8*qhalf+7
-        int i = 0;
-        for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
-            const int s = i & 1, u = i >> 1;
-            if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
-            const uint64_t c = t * kNT + n;
-            const bool valid = c < G.n_cols;
-            const uint64_t cb = valid ? (col_base(t * kNT, G) | S.pd[n]) : 0;
-            float2 v[32];
-#pragma unroll
-            for (int m = 0; m < 32; ++m) {
-                const int j = qhalf * 32 + m;
-                v[m] = valid ? sv[cb + G.off[j]] : make_float2(0.f, 0.f);
-            }
-            unsigned char *sb = sB0 + s * kBStage;
-#pragma unroll
-            for (int qq = 0; qq < 8; ++qq) {
-                const int q = qhalf * 8 + qq;     // members 4q .. 4q+3 = K 8q .. 8q+7
-                const float2 a0 = v[4 * qq], a1 = v[4 * qq + 1], a2 = v[4 * qq + 2], a3 = v[4 * qq + 3];
-                if constexpr (P == TF32) {
-                    const int kb = q >> 2, ch = 2 * (q & 3);
-                    uint4 w0 = make_uint4(to_tf32(a0.x), to_tf32(a0.y), to_tf32(a1.x), to_tf32(a1.y));
-                    uint4 w1 = make_uint4(to_tf32(a2.x), to_tf32(a2.y), to_tf32(a3.x), to_tf32(a3.y));
-                    *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch)) = w0;
-                    *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch + 1)) = w1;
-                } else {
-                    const int kb = q >> 3, ch = q & 7;
-                    uint4 hi, lo;
-                    split_bf16(a0.x, a0.y, hi.x, lo.x);
-                    split_bf16(a1.x, a1.y, hi.y, lo.y);
-                    split_bf16(a2.x, a2.y, hi.z, lo.z);
-                    split_bf16(a3.x, a3.y, hi.w, lo.w);
-                    *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch)) = hi;
-                    *reinterpret_cast<uint4 *>(sb + kBStage / 2 + sw128(kb, n, ch)) = lo;
+        if constexpr (VEC4) {
+            // qubit 0 is not a target: lane n takes column n (8-byte loads, consecutive
+            // lanes on consecutive columns, 32 loads in flight per thread) and stores
+            // whole 16-byte chunks of the swizzled operand, free of bank conflicts
+            const int n = threadIdx.x & (kNT - 1);          // column within the tile
+            const int qhalf = threadIdx.x >> 7;             // member quads 8*qhalf .. 8*qhalf+7
+            int i = 0;
+            for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+                const int s = i & 1, u = i >> 1;
+                if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
+                const uint64_t c = t * kNT + n;
+                const bool valid = c < G.n_cols;
+                const uint64_t cb = valid ? (col_base(t * kNT, G) | S.pd[n]) : 0;
+                float2 v[32];
+    #pragma unroll
+                for (int m = 0; m < 32; ++m) {
+                    const int j = qhalf * 32 + m;
+                    v[m] = valid ? sv[cb + G.off[j]] : make_float2(0.f, 0.f);
                 }
+                unsigned char *sb = sB0 + s * kBStage;
+    #pragma unroll
+                for (int qq = 0; qq < 8; ++qq) {
+                    const int q = qhalf * 8 + qq;     // members 4q .. 4q+3 = K 8q .. 8q+7
+                    const float2 a0 = v[4 * qq], a1 = v[4 * qq + 1], a2 = v[4 * qq + 2], a3 = v[4 * qq + 3];
+                    if constexpr (P == TF32) {
+                        const int kb = q >> 2, ch = 2 * (q & 3);
+                        uint4 w0 = make_uint4(to_tf32(a0.x), to_tf32(a0.y), to_tf32(a1.x), to_tf32(a1.y));
+                        uint4 w1 = make_uint4(to_tf32(a2.x), to_tf32(a2.y), to_tf32(a3.x), to_tf32(a3.y));
+                        *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch)) = w0;
+                        *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch + 1)) = w1;
+                    } else {
+                        const int kb = q >> 3, ch = q & 7;
+                        uint4 hi, lo;
+                        split_bf16(a0.x, a0.y, hi.x, lo.x);
+                        split_bf16(a1.x, a1.y, hi.y, lo.y);
+                        split_bf16(a2.x, a2.y, hi.z, lo.z);
+                        split_bf16(a3.x, a3.y, hi.w, lo.w);
+                        *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch)) = hi;
+                        *reinterpret_cast<uint4 *>(sb + kBStage / 2 + sw128(kb, n, ch)) = lo;
+                    }
+                }
+                fence_proxy_async();
+                mbar_arrive(smem_u32(&S.full[s]));
             }
-            fence_proxy_async();
-            mbar_arrive(smem_u32(&S.full[s]));
+        } else {
+            // Each thread loads 16 pairs of adjacent amplitudes of the tile in address
+            // order (lane-consecutive 16-byte loads: every warp load is one contiguous
+            // 512-byte run), then scatters each amplitude to its (column, member) slot
+            // of the K-major swizzled operand, rounded to TF32 or split into BF16.
+            int i = 0;
+            for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+                const int s = i & 1, u = i >> 1;
+                if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
+                const uint64_t tb = col_base(t * kNT, G);
+                const uint64_t tcol = t * kNT;
+                float4 v[16];
+    #pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const int a = 2 * ((int)threadIdx.x + kProd * r);
+                    const int ij = S.ij_lo[a & 127] | S.ij_hi[a >> 7];
+                    v[r] = (tcol + (ij & 127) < G.n_cols)
+                               ? *reinterpret_cast<const float4 *>(sv + (tb | S.adr_lo[a & 127] | S.adr_hi[a >> 7]))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                unsigned char *sb = sB0 + s * kBStage;
+    #pragma unroll
+                for (int r = 0; r < 16; ++r) {
+    #pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int a = 2 * ((int)threadIdx.x + kProd * r) + h;
+                        const int ij = S.ij_lo[a & 127] | S.ij_hi[a >> 7];
+                        const int col = ij & 127, j = ij >> 7;
+                        const float re = h ? v[r].z : v[r].x, im = h ? v[r].w : v[r].y;
+                        if constexpr (P == TF32) {
+                            // K = 2j, 2j+1: K-block j/16, chunk (j%16)/2, 8-byte half j%2
+                            *reinterpret_cast<uint2 *>(sb + sw128(j >> 4, col, (j & 15) >> 1) + (j & 1) * 8) =
+                                make_uint2(to_tf32(re), to_tf32(im));
+                        } else {
+                            // K = 2j, 2j+1: K-block j/32, chunk (j%32)/4, 4-byte quarter j%4
+                            uint32_t hi, lo;
+                            split_bf16(re, im, hi, lo);
+                            const uint32_t o = sw128(j >> 5, col, (j & 31) >> 2) + (j & 3) * 4;
+                            *reinterpret_cast<uint32_t *>(sb + o) = hi;
+                            *reinterpret_cast<uint32_t *>(sb + kBStage / 2 + o) = lo;
+                        }
+                    }
+                }
+                fence_proxy_async();
+                mbar_arrive(smem_u32(&S.full[s]));
+            }
         }
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------

@@ -213,6 +213,67 @@ sv_status_t sync_results(sv_ctx *h, int count) {
     return cuda_status(cudaStreamSynchronize(h->stream));
 }
 
+// Tensor-core blocks whose targets all sit at or above this qubit read 64 rows
+// that are at least 1 MiB apart (complex64); measured on GB300 they run at about
+// half the speed of blocks with a lower target.
+constexpr int kFarQubit = 17;
+
+// Qubit relabelling for a fused run (Sec. II-C, qubit reordering, applied on one
+// GPU): disjoint swaps (low, high) chosen greedily so that as many wide blocks
+// as possible get a target below kFarQubit. Returns the pairs (empty when the
+// saving does not pay for the two extra passes) and the map logical -> physical.
+void choose_layout(const std::vector<svf::Item> &items, int n, std::vector<int> &pairs, std::vector<int> &map) {
+    map.resize(n);
+    for (int q = 0; q < n; ++q) map[q] = q;
+    pairs.clear();
+    if (n <= kFarQubit) return;
+    std::vector<const std::vector<int> *> wide;
+    for (const svf::Item &it : items)
+        if (!it.passthrough && it.qubits.size() >= 5) wide.push_back(&it.qubits);
+    auto far_count = [&](const std::vector<int> &m) {
+        int c = 0;
+        for (const std::vector<int> *qs : wide) {
+            int lo = 1 << 30;
+            for (int q : *qs) lo = std::min(lo, m[q]);
+            c += lo >= kFarQubit;
+        }
+        return c;
+    };
+    const int before = far_count(map);
+    int cur = before;
+    std::vector<char> used(n, 0);
+    for (;;) {
+        int best = cur, bl = -1, bh = -1;
+        for (int l = 0; l < kFarQubit; ++l) {
+            if (used[l]) continue;
+            for (int hq = kFarQubit; hq < n; ++hq) {
+                if (used[hq]) continue;
+                std::vector<int> m = map;
+                for (int q = 0; q < n; ++q) {
+                    if (map[q] == l) m[q] = hq;
+                    else if (map[q] == hq) m[q] = l;
+                }
+                const int c = far_count(m);
+                if (c < best) { best = c; bl = l; bh = hq; }
+            }
+        }
+        if (bl < 0 || (int)pairs.size() / 2 >= 18) break;
+        for (int q = 0; q < n; ++q) {
+            if (map[q] == bl) map[q] = bh;
+            else if (map[q] == bh) map[q] = bl;
+        }
+        used[bl] = used[bh] = 1;
+        pairs.push_back(bl);
+        pairs.push_back(bh);
+        cur = best;
+    }
+    // a far block costs about 1.5 near blocks more; the two swap passes about 2
+    if (3 * (before - cur) < 4) {
+        pairs.clear();
+        for (int q = 0; q < n; ++q) map[q] = q;
+    }
+}
+
 sv_status_t qubit_mask(const sv_ctx *h, const int *qubits, int m, uint64_t *mask) {
     if (!qubits || m < 1 || m > h->n) return SV_ERR_INVALID_ARGUMENT;
     uint64_t s = 0;
@@ -339,6 +400,22 @@ sv_status_t sv_apply_matrix(sv_handle_t h, const int *targets, int n_targets, co
                       SV_PREC_NATIVE);
 }
 
+sv_status_t sv_swap_index_bits(sv_handle_t h, const int *bit_pairs, int n_pairs) {
+    if (!h || !bit_pairs || n_pairs < 1 || n_pairs > 18) return SV_ERR_INVALID_ARGUMENT;
+    int a[18], b[18];
+    uint64_t seen = 0;
+    for (int k = 0; k < n_pairs; ++k) {
+        a[k] = bit_pairs[2 * k];
+        b[k] = bit_pairs[2 * k + 1];
+        if (a[k] < 0 || a[k] >= h->n || b[k] < 0 || b[k] >= h->n || a[k] == b[k] || ((seen >> a[k]) & 1u) ||
+            ((seen >> b[k]) & 1u))
+            return SV_ERR_INVALID_ARGUMENT;
+        seen |= (1ull << a[k]) | (1ull << b[k]);
+    }
+    DeviceGuard dg(h->device);
+    return cuda_status(svk::launch_swap(lctx(h), h->dt, h->sv, h->n, a, b, n_pairs));
+}
+
 sv_status_t sv_fuse_plan(const sv_gate_t *gates, int n_gates, int n_qubits, int max_fused_qubits, int max_blocks,
                          int *n_blocks_out, int *block_k, int *block_targets, double *block_matrices) {
     if ((!gates && n_gates > 0) || n_gates < 0 || !n_blocks_out || n_qubits < 1 || n_qubits > SV_MAX_QUBITS)
@@ -418,18 +495,35 @@ sv_status_t sv_apply_fused(sv_handle_t h, const sv_gate_t *gates, int n_gates, i
     sv_status_t s = svf::fuse(gates, n_gates, h->n, max_fused_qubits, items);
     if (s != SV_OK) return s;
     DeviceGuard dg(h->device);
+    std::vector<int> pairs, map;
+    if (prec != SV_PREC_NATIVE) choose_layout(items, h->n, pairs, map);
+    else {
+        map.resize(h->n);
+        for (int q = 0; q < h->n; ++q) map[q] = q;
+    }
+    const int npairs = (int)pairs.size() / 2;
+    if (npairs > 0) {
+        s = sv_swap_index_bits(h, pairs.data(), npairs);
+        if (s != SV_OK) return s;
+    }
     for (const svf::Item &it : items) {
         if (it.passthrough) {
             const sv_gate_t &g = gates[it.gate];
-            s = apply_gate(h, make_gate(g.targets, g.n_targets, g.controls, g.control_values, g.n_controls, g.matrix,
-                                        0),
-                           prec);
+            Gate gg = make_gate(g.targets, g.n_targets, g.controls, g.control_values, g.n_controls, g.matrix, 0);
+            for (int &q : gg.t) q = map[q];
+            for (int &q : gg.c) q = map[q];
+            s = apply_gate(h, gg, prec);
         } else {
             Gate g;
             g.t = it.qubits;
+            for (int &q : g.t) q = map[q];
             g.m = it.m;
             s = apply_gate(h, g, prec);
         }
+        if (s != SV_OK) return s;
+    }
+    if (npairs > 0) {
+        s = sv_swap_index_bits(h, pairs.data(), npairs);
         if (s != SV_OK) return s;
     }
     if (n_fused_out) *n_fused_out = (int)items.size();
@@ -495,6 +589,46 @@ sv_status_t sv_expectation_pauli(sv_handle_t h, const int *paulis, const int *si
         }
     }
     return flush();
+}
+
+sv_status_t sv_apply_pauli_rotation(sv_handle_t h, double theta, const int *paulis, const int *sites, int n_sites) {
+    if (!h || n_sites < 0 || (n_sites > 0 && (!paulis || !sites)) || !std::isfinite(theta))
+        return SV_ERR_INVALID_ARGUMENT;
+    uint64_t x = 0, z = 0, seen = 0;
+    int ny = 0;
+    for (int i = 0; i < n_sites; ++i) {
+        const int p = paulis[i], q = sites[i];
+        if (p < 0 || p > 3 || q < 0 || q >= h->n || ((seen >> q) & 1u)) return SV_ERR_INVALID_ARGUMENT;
+        seen |= 1ull << q;
+        if (p == SV_PAULI_X || p == SV_PAULI_Y) x |= 1ull << q;
+        if (p == SV_PAULI_Z || p == SV_PAULI_Y) z |= 1ull << q;
+        ny += p == SV_PAULI_Y;
+    }
+    DeviceGuard dg(h->device);
+    return cuda_status(svk::launch_pauli_rotation(lctx(h), h->dt, h->sv, h->n, x, z, ny & 3, theta));
+}
+
+sv_status_t sv_sample(sv_handle_t h, const double *randnums, int n_samples, int64_t *out) {
+    if (!h || n_samples < 0 || (n_samples > 0 && (!randnums || !out))) return SV_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < n_samples; ++i)
+        if (!(randnums[i] >= 0.0 && randnums[i] < 1.0)) return SV_ERR_INVALID_ARGUMENT;
+    if (n_samples == 0) return SV_OK;
+    DeviceGuard dg(h->device);
+    // workspace: 2^20 segment sums (8 MiB), then chunks of random numbers and outcomes
+    constexpr int kChunk = 1 << 18;
+    double *d_seg = reinterpret_cast<double *>(h->d_mat);
+    double *d_r = d_seg + (1 << 20);
+    long long *d_o = reinterpret_cast<long long *>(d_r + kChunk);
+    for (int b = 0; b < n_samples; b += kChunk) {
+        const int m = std::min(kChunk, n_samples - b);
+        if (cudaMemcpyAsync(d_r, randnums + b, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+            return SV_ERR_CUDA;
+        if (svk::launch_sample(lctx(h), h->dt, h->sv, h->n, d_r, m, d_seg, d_o) != cudaSuccess) return SV_ERR_CUDA;
+        if (cudaMemcpyAsync(out + b, d_o, sizeof(long long) * m, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return SV_ERR_CUDA;
+    }
+    return SV_OK;
 }
 
 sv_status_t sv_measure_probs(sv_handle_t h, const int *qubits, int n_qubits, double *p_even, double *p_odd) {

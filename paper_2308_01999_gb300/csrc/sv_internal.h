@@ -48,6 +48,13 @@ cudaError_t launch_diag(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, cons
 cudaError_t launch_perm(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, const GroupGeom &G,
                         const int *tpos, int k, const int *perm, const double *d);
 
+// Index-bit swap: bits a[k] <-> b[k] of every amplitude index (disjoint pairs, np <= 18).
+cudaError_t launch_swap(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, const int *a, const int *b, int np);
+
+// psi <- exp(i theta P) psi, P given by its X|Y mask x, Z|Y mask z and Y count ny.
+cudaError_t launch_pauli_rotation(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t x, uint64_t z, int ny,
+                                  double theta);
+
 // ---- reductions (k_reduce.cu) ----
 struct PauliPass {
     int S;              // strings in this pass (1..8)
@@ -65,6 +72,11 @@ cudaError_t launch_parity(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int
                           double *d_partials, int max_partial_blocks, double *d_out);
 cudaError_t launch_collapse(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t mask,
                             int parity, double scale);
+// Sampler: basis indices at which the cumulative probability first exceeds
+// r * total, for each r. d_seg: workspace of at least 2^20 doubles; d_r / d_out:
+// n_samples doubles / int64 (device). Segment size 2^max(12, n - 20).
+cudaError_t launch_sample(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int n, const double *d_r, int n_samples,
+                          double *d_seg, long long *d_out);
 cudaError_t launch_set_basis(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t index);
 
 // ---- tensor-core fused apply (k_tc.cu) ----

@@ -40,7 +40,7 @@ EXPORTED = [
     "sv_expectation_pauli", "sv_measure_probs", "sv_collapse", "sv_measure", "sv_norm2",
     "sv_check_device_status", "sv_launch_count", "sv_status_string", "sv_expectation_pauli_noalloc",
     "sv_batch_create", "sv_batch_destroy", "sv_batch_compile", "sv_batch_info", "sv_batch_launch",
-    "sv_batch_results",
+    "sv_batch_results", "sv_swap_index_bits", "sv_apply_pauli_rotation", "sv_sample",
 ]
 
 
@@ -88,6 +88,9 @@ def lib():
             "sv_batch_info": [_VP, _I, _I, _I, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
             "sv_batch_launch": [_VP, C.c_int, _VP, C.c_int],
             "sv_batch_results": [_VP, _D, C.c_int],
+            "sv_swap_index_bits": [_VP, _I, C.c_int],
+            "sv_apply_pauli_rotation": [_VP, C.c_double, _I, _I, C.c_int],
+            "sv_sample": [_VP, _D, C.c_int, C.POINTER(C.c_int64)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -245,6 +248,30 @@ def sv_expectation_pauli_noalloc(n_qubits: int, dtype: int, d_state_ptr: int, st
     return out
 
 
+def sv_swap_index_bits(h: int, pairs):
+    """Exchange index bits a <-> b for each (a, b) in `pairs` (disjoint)."""
+    p, pp = _ints([q for ab in pairs for q in ab])
+    _check(lib().sv_swap_index_bits(_VP(h), pp, len(pairs)), "sv_swap_index_bits")
+
+
+def sv_apply_pauli_rotation(h: int, theta: float, paulis, sites):
+    """psi <- exp(i theta P) psi for the Pauli string (paulis[i] on qubit sites[i])."""
+    p, pp = _ints(paulis)
+    s, sp = _ints(sites)
+    if p.size != s.size:
+        raise ValueError("paulis and sites must have the same length")
+    _check(lib().sv_apply_pauli_rotation(_VP(h), float(theta), pp, sp, int(p.size)), "sv_apply_pauli_rotation")
+
+
+def sv_sample(h: int, randnums) -> np.ndarray:
+    """Basis indices sampled from |psi|^2 by inverting the cumulative distribution."""
+    r = np.ascontiguousarray(np.asarray(randnums, dtype=np.float64).reshape(-1))
+    out = np.zeros(r.size, dtype=np.int64)
+    _check(lib().sv_sample(_VP(h), r.ctypes.data_as(_D), int(r.size), out.ctypes.data_as(C.POINTER(C.c_int64))),
+           "sv_sample")
+    return out
+
+
 def sv_measure_probs(h: int, qubits):
     q, qp = _ints(qubits)
     a, b = C.c_double(), C.c_double()
@@ -342,6 +369,15 @@ class StateVector:
     def expectation_z_all(self):
         n = self.n
         return sv_expectation_pauli(self.handle, np.full((n, 1), 3, np.int32), np.arange(n, dtype=np.int32)[:, None])
+
+    def pauli_rotation(self, theta, paulis, sites):
+        sv_apply_pauli_rotation(self.handle, theta, paulis, sites)
+
+    def sample(self, randnums):
+        return sv_sample(self.handle, randnums)
+
+    def swap_index_bits(self, pairs):
+        sv_swap_index_bits(self.handle, pairs)
 
     def measure_probs(self, qubits):
         return sv_measure_probs(self.handle, qubits)

@@ -232,3 +232,63 @@ def test_oracle_rejects_bad_arguments():
         orc.apply_gate(psi, [0, 0], np.eye(4))
     with pytest.raises(ValueError):
         orc.expect_pauli(psi, [1, 1], [2, 2])
+
+
+@pytest.mark.parametrize("n", [1, 3, 5])
+def test_pauli_rotation_equals_matrix_exponential(n):
+    import scipy.linalg
+    rng = gen.rng_for(60 + n)
+    paulis, sites = gen.random_pauli_strings(n, 6, rng)
+    for ps, ss in zip(paulis, sites):
+        theta = float(rng.uniform(-3, 3))
+        psi = gen.random_state(n, 61 + n)
+        want = scipy.linalg.expm(1j * theta * np_ref.pauli_operator(n, ps, ss)) @ psi
+        orc.pauli_rotation(psi, ps, ss, theta)
+        np.testing.assert_allclose(psi, want, atol=1e-13, rtol=0)
+
+
+def test_pauli_rotation_closed_forms():
+    # exp(i t Z) = diag(e^{it}, e^{-it}); exp(i t X) = [[cos t, i sin t], [i sin t, cos t]];
+    # t = pi/2 gives i P; rotations about the same string add their angles
+    t = 0.37
+    psi = gen.random_state(3, 9)
+    ref = psi.copy()
+    orc.pauli_rotation(psi, [3], [1], t)
+    orc.apply_gate(ref, [1], np.diag([np.exp(1j * t), np.exp(-1j * t)]))
+    np.testing.assert_allclose(psi, ref, atol=1e-15)
+    psi = gen.random_state(3, 10)
+    ref = psi.copy()
+    orc.pauli_rotation(psi, [1], [2], t)
+    orc.apply_gate(ref, [2], np.array([[np.cos(t), 1j * np.sin(t)], [1j * np.sin(t), np.cos(t)]]))
+    np.testing.assert_allclose(psi, ref, atol=1e-15)
+    psi = gen.random_state(4, 11)
+    ref = psi.copy()
+    orc.pauli_rotation(psi, [2, 1, 3], [0, 2, 3], np.pi / 2)
+    np.testing.assert_allclose(psi, 1j * (np_ref.pauli_operator(4, [2, 1, 3], [0, 2, 3]) @ ref), atol=1e-14)
+    a = gen.random_state(4, 12)
+    b = a.copy()
+    orc.pauli_rotation(a, [2, 3], [1, 3], 0.4)
+    orc.pauli_rotation(a, [2, 3], [1, 3], 0.9)
+    orc.pauli_rotation(b, [2, 3], [1, 3], 1.3)
+    np.testing.assert_allclose(a, b, atol=1e-14)
+
+
+def test_sampler_closed_forms_and_frequencies():
+    n = 5
+    basis = np.zeros(1 << n, dtype=np.complex128)
+    basis[13] = 1
+    assert (orc.sample(basis, [0.0, 0.3, 0.999]) == 13).all()
+    ghz = orc.run_circuit(gen.ghz_circuit(n), n)
+    assert list(orc.sample(ghz, [0.1, 0.49, 0.51, 0.9])) == [0, 0, 31, 31]
+    # the draw inverts the cumulative probability relative to the norm
+    assert list(orc.sample(2.0 * ghz, [0.1, 0.49, 0.51, 0.9])) == [0, 0, 31, 31]
+    uni = orc.run_circuit([gen.Gate((q,), gen.gate_h()) for q in range(n)], n)
+    r = np.array([0.0, 0.2, 0.5, 0.77, 0.999])
+    assert list(orc.sample(uni, r)) == list(np.floor(r * 32 + 1e-9).astype(int))
+    # frequencies of many uniform draws follow |psi_i|^2 (chi-square at the 0.1 % level)
+    psi = gen.random_state(4, 3)
+    p = np.abs(psi) ** 2
+    draws = orc.sample(psi, gen.rng_for(4).uniform(size=40000))
+    counts = np.bincount(draws, minlength=16)
+    chi2 = np.sum((counts - 40000 * p) ** 2 / (40000 * p))
+    assert chi2 < 37.7   # chi-square, 15 degrees of freedom, p = 0.001

@@ -31,6 +31,10 @@ MUTATIONS = [
     ("collapse without sqrt", "const double scale = 1.0 / sqrt(prob);", "const double scale = 1.0 / prob;"),
     ("parity from one qubit", "for (int t = 0; t < m; ++t) p ^= (int)((i >> qubits[t]) & 1u);",
      "p = (int)((i >> qubits[0]) & 1u);"),
+    ("rotation sign", "psi[i] = c * psi[i] + I * sn * phi[i];", "psi[i] = c * psi[i] - I * sn * phi[i];"),
+    ("rotation without cosine", "psi[i] = c * psi[i] + I * sn * phi[i];", "psi[i] = psi[i] + I * sn * phi[i];"),
+    ("sampler boundary", "if (cum[mid] > target) hi = mid;", "if (cum[mid] >= target) hi = mid;"),
+    ("sampler unscaled target", "const double target = randnums[t] * acc;", "const double target = randnums[t];"),
 ]
 
 
@@ -52,6 +56,9 @@ def _pin_calls():
     calls.append(("identity", pins.test_identity_string_is_the_norm))
     calls.append(("measure_ghz", pins.test_measurement_ghz_and_collapse))
     calls.append(("measure_sum", pins.test_measurement_probabilities_sum_to_norm))
+    calls.append(("rotation_expm", lambda: pins.test_pauli_rotation_equals_matrix_exponential(3)))
+    calls.append(("rotation_closed", pins.test_pauli_rotation_closed_forms))
+    calls.append(("sampler", pins.test_sampler_closed_forms_and_frequencies))
     return calls
 
 
@@ -75,7 +82,7 @@ def test_every_planted_mistake_fails_a_pin(name, before, after):
         so = _build_mutant(tmp, before, after)
         mut = ctypes.CDLL(so)
         for fn in ("orc_threads", "orc_apply", "orc_expect_pauli", "orc_parity_probs",
-                   "orc_collapse", "orc_norm2"):
+                   "orc_collapse", "orc_norm2", "orc_pauli_rotation", "orc_sample"):
             src_fn, dst_fn = getattr(real, fn), getattr(mut, fn)
             dst_fn.argtypes, dst_fn.restype = src_fn.argtypes, src_fn.restype
         orc._lib = mut
