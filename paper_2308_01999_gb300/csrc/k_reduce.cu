@@ -422,6 +422,148 @@ cudaError_t sample_t(const LaunchCtx &L, const void *sv, int n, const double *d_
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// <Z_q> for every qubit in one pass: with p_i = |psi_i|^2 and S_q the sum of
+// p_i over indices with bit q set, <Z_q> = sum_i p_i - 2 S_q. The state is cut
+// into chunks of 8 amplitudes; block b owns the aligned chunk range
+// [b 2^m, (b+1) 2^m) and thread t the chunks b 2^m + j 2^mt + t. So amplitude
+// bits 0..2 vary inside a chunk (three partial sums), bits 3..3+mt-1 are the
+// thread's (its whole total counts for them), bits 3+mt..3+m-1 follow the loop
+// counter j (one partial sum each) and the bits above are fixed per block.
+// FP32 over 16 chunks, FP64 beyond; partial rows [kZMax + 1] per block are
+// summed in a fixed order by k_zall_finish.
+// ---------------------------------------------------------------------------
+constexpr int kZMax = 40;
+constexpr int kZJ = 16;   // most loop-counter bits
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_zall(const typename CT<R>::T *__restrict__ sv, int n, int m, int mt, double *__restrict__ partials) {
+    using C = typename CT<R>::T;
+    __shared__ double red[kThreads / 32];
+    __shared__ double row[kZMax + 1];
+    const int mj = m - mt;
+    const int t = threadIdx.x;
+    const bool active = t < (1 << mt);
+    const uint64_t c0 = (uint64_t)blockIdx.x << m;
+    double dT = 0.0, dB[3] = {0.0, 0.0, 0.0}, dJ[kZJ];
+    R fT = R(0), fB[3] = {R(0), R(0), R(0)}, fJ[kZJ];
+#pragma unroll
+    for (int q = 0; q < kZJ; ++q) { dJ[q] = 0.0; fJ[q] = R(0); }
+    int cnt = 0;
+    const uint64_t nj = 1ull << mj;
+    for (uint64_t j = 0; active && j < nj; ++j) {
+        const uint64_t c = c0 + (j << mt) + t;
+        R p[8];
+        if constexpr (sizeof(R) == 4) {
+            const float4 *src = reinterpret_cast<const float4 *>(sv) + 4 * c;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float4 f = src[h];
+                p[2 * h] = f.x * f.x + f.y * f.y;
+                p[2 * h + 1] = f.z * f.z + f.w * f.w;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const C a = sv[8 * c + e];
+                p[e] = a.x * a.x + a.y * a.y;
+            }
+        }
+        const R tot = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+        fT += tot;
+        fB[0] += (p[1] + p[3]) + (p[5] + p[7]);
+        fB[1] += (p[2] + p[3]) + (p[6] + p[7]);
+        fB[2] += (p[4] + p[5]) + (p[6] + p[7]);
+#pragma unroll
+        for (int q = 0; q < kZJ; ++q)
+            if (q < mj && ((j >> q) & 1u)) fJ[q] += tot;
+        if (++cnt == 16) {
+            dT += (double)fT;
+            fT = R(0);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) { dB[q] += (double)fB[q]; fB[q] = R(0); }
+#pragma unroll
+            for (int q = 0; q < kZJ; ++q) { dJ[q] += (double)fJ[q]; fJ[q] = R(0); }
+            cnt = 0;
+        }
+    }
+    dT += (double)fT;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) dB[q] += (double)fB[q];
+#pragma unroll
+    for (int q = 0; q < kZJ; ++q) dJ[q] += (double)fJ[q];
+    // block sums in a fixed order: warp shuffles, then warps in order
+    auto bsum = [&](double v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if ((t & 31) == 0) red[t >> 5] = v;
+        __syncthreads();
+        double a = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) a += red[w];
+        return a;
+    };
+    const double total = bsum(dT);
+    for (int q = 0; q < 3; ++q) {
+        const double v = bsum(dB[q]);
+        if (t == 0) row[q] = v;
+    }
+    for (int b = 0; b < mt; ++b) {
+        const double v = bsum(((t >> b) & 1) ? dT : 0.0);
+        if (t == 0) row[3 + b] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < kZJ; ++q) {
+        if (q < mj) {                       // mj is the same for every thread
+            const double v = bsum(dJ[q]);
+            if (t == 0) row[3 + mt + q] = v;
+        }
+    }
+    if (t == 0) {
+        const uint64_t base = c0 << 3;
+        for (int q = 3 + m; q < n; ++q) row[q] = ((base >> q) & 1u) ? total : 0.0;
+        for (int q = n; q < kZMax; ++q) row[q] = 0.0;
+        row[kZMax] = total;
+    }
+    __syncthreads();
+    for (int q = t; q <= kZMax; q += kThreads) partials[(size_t)blockIdx.x * (kZMax + 1) + q] = row[q];
+}
+
+// out[q] = total - 2 S_q for q < n, out[n] = total; partials summed in block order
+__global__ void __launch_bounds__(64) k_zall_finish(const double *__restrict__ partials, int nblocks, int n,
+                                                    double *__restrict__ out) {
+    const int q = threadIdx.x;
+    if (q > kZMax) return;
+    double a = 0.0, tt = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        a += partials[(size_t)b * (kZMax + 1) + q];
+        tt += partials[(size_t)b * (kZMax + 1) + kZMax];
+    }
+    if (q < n) out[q] = tt - 2.0 * a;
+    if (q == kZMax) out[n] = tt;
+}
+
+template <typename R>
+cudaError_t zall_t(const LaunchCtx &L, const void *sv, int n, double *d_partials, int maxb, double *d_out) {
+    using C = typename CT<R>::T;
+    // m = log2(chunks per block): about 512 blocks, at least 2^min(n-3, 8) chunks each, at most kZJ loop bits
+    int m = n - 3 - 9;
+    const int lo = (n - 3) < 8 ? (n - 3) : 8;
+    if (m < lo) m = lo;
+    if (m > 8 + kZJ) m = 8 + kZJ;
+    const int mt = m < 8 ? m : 8;
+    const uint64_t blocks = 1ull << (n - 3 - m);
+    if (blocks * (kZMax + 1) > (uint64_t)maxb * 8) return cudaErrorInvalidValue;
+    k_zall<R><<<(unsigned)blocks, kThreads, 0, L.stream>>>(reinterpret_cast<const C *>(sv), n, m, mt, d_partials);
+    ++*L.launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_zall_finish<<<1, 64, 0, L.stream>>>(d_partials, (int)blocks, n, d_out);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_pauli(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int n, const PauliPass &P,
@@ -450,6 +592,13 @@ cudaError_t launch_sample(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int
     if (n < 1 || n_samples < 1) return cudaErrorInvalidValue;
     return dt == SV_C64 ? sample_t<float>(L, sv, n, d_r, n_samples, d_seg, d_out)
                         : sample_t<double>(L, sv, n, d_r, n_samples, d_seg, d_out);
+}
+
+cudaError_t launch_zall(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int n, double *d_partials,
+                        int max_partial_blocks, double *d_out) {
+    if (n < 3 || n > kZMax) return cudaErrorInvalidValue;
+    return dt == SV_C64 ? zall_t<float>(L, sv, n, d_partials, max_partial_blocks, d_out)
+                        : zall_t<double>(L, sv, n, d_partials, max_partial_blocks, d_out);
 }
 
 cudaError_t launch_set_basis(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t index) {

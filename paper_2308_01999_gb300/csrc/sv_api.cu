@@ -551,6 +551,19 @@ sv_status_t sv_expectation_pauli(sv_handle_t h, const int *paulis, const int *si
     }
     if (n_strings == 0) return SV_OK;
     DeviceGuard dg(h->device);
+    // strings of identities and at most one Z: all of them from one <Z_q> pass
+    bool single_z = h->n >= 3;
+    for (int s = 0; s < n_strings && single_z; ++s) single_z = strs[s].x == 0 && __builtin_popcountll(strs[s].z) <= 1;
+    if (single_z && n_strings >= 2) {
+        if (svk::launch_zall(lctx(h), h->dt, h->sv, h->n, h->d_partials, h->max_partial_blocks, h->d_results) !=
+            cudaSuccess)
+            return SV_ERR_CUDA;
+        sv_status_t st = sync_results(h, h->n + 1);
+        if (st != SV_OK) return st;
+        for (int s = 0; s < n_strings; ++s)
+            out[s] = strs[s].z ? h->h_results[__builtin_ctzll(strs[s].z)] : h->h_results[h->n];
+        return SV_OK;
+    }
     // strings with the same X/Y mask share a pass over the state
     std::map<uint64_t, std::vector<int>> by_x;
     for (int s = 0; s < n_strings; ++s) by_x[strs[s].x].push_back(s);

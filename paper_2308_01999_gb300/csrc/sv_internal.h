@@ -72,6 +72,9 @@ cudaError_t launch_parity(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int
                           double *d_partials, int max_partial_blocks, double *d_out);
 cudaError_t launch_collapse(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n, uint64_t mask,
                             int parity, double scale);
+// d_out[q] = <Z_q> for q < n and d_out[n] = <psi|psi>, one pass (3 <= n <= 40).
+cudaError_t launch_zall(const LaunchCtx &L, sv_dtype_t dt, const void *sv, int n, double *d_partials,
+                        int max_partial_blocks, double *d_out);
 // Sampler: basis indices at which the cumulative probability first exceeds
 // r * total, for each r. d_seg: workspace of at least 2^20 doubles; d_r / d_out:
 // n_samples doubles / int64 (device). Segment size 2^max(12, n - 20).

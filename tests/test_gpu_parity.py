@@ -316,3 +316,23 @@ def test_invalid_arguments_are_rejected(env):
     s.apply([0], gen.gate_h())
     assert s.launches() == n0 + 1
     s.check()
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("n", [3, 4, 11, 12, 13, 21, 24])
+def test_z_expectations_of_every_qubit_in_one_pass(env, name, n):
+    """Strings of identities and single Z (the <Z_q> request) take the one-pass
+    kernel; compare with the oracle, in any order, with repeats and the norm."""
+    init = gen.random_state(n, 500 + n)
+    psi, s = make_state(env, n, name, init)
+    ref = host(psi)
+    z = s.expectation_z_all()
+    assert_exp(z, orc.expect_z_all(ref), name, f"<Z> n={n}")
+    order = [n - 1, 0, n // 2, 0]
+    paulis = np.zeros((len(order) + 1, n), np.int32)
+    for r, q in enumerate(order):
+        paulis[r, q] = 3
+    sites = np.tile(np.arange(n, dtype=np.int32), (paulis.shape[0], 1))
+    got = s.expectation_pauli(paulis, sites)
+    want = [orc.expect_pauli(ref, p, q).real for p, q in zip(paulis, sites)]
+    assert_exp(got, want, name, "mixed single-Z strings")
