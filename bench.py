@@ -40,9 +40,11 @@ DEPTH = 40
 AMP_BYTES = 8
 METRIC = "gate-apply HBM GB/s (28-qubit complex64 random circuit, unfused, one gate per launch)"
 UNIT = "GB/s"
-WORKLOAD = ("28-qubit random circuit, complex64 state (2 GiB) resident in HBM, depth 40: Haar SU(2) on all "
-            "qubits + CZ/CNOT/CRZ on 14 random disjoint pairs per layer, one gate per launch, then <Z_q> for all "
-            "28 qubits, 8 random Pauli strings and a 2-qubit parity measurement")
+def workload_name():
+    return (f"{N_QUBITS}-qubit random circuit, complex64 state ({(8 << N_QUBITS) / 2**30:g} GiB) resident in HBM, "
+            f"depth 40: Haar SU(2) on all qubits + CZ/CNOT/CRZ on {N_QUBITS // 2} random disjoint pairs per layer, "
+            f"one gate per launch, then <Z_q> for all {N_QUBITS} qubits, 8 random Pauli strings and a 2-qubit "
+            "parity measurement")
 FRACTION = {"su2": 1.0, "cnot": 0.5, "crz": 0.5, "cz": 0.25}
 
 
@@ -222,7 +224,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS},
+        "data": "synthetic", "config": {"workload": workload_name(), "n_qubits": N_QUBITS},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -339,16 +341,17 @@ def run_ours(args):
     cpu = cpu_baseline(gates) if world == 1 and not args.no_cpu_baseline else None
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
+    if os.path.exists(tfile) and N_QUBITS == 28:
         with open(tfile) as f:
             traffic = json.load(f).get("k_dense_1q_per_launch_bytes")
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "depth": DEPTH, "gates_per_step": n_gates,
+        "config": {"workload": workload_name(), "n_qubits": N_QUBITS, "depth": DEPTH, "gates_per_step": n_gates,
                    "state_bytes": AMP_BYTES << N_QUBITS, "bytes_per_step": nbytes,
-                   "l2": "no flush: the 2 GiB state exceeds the 129 MB L2", "parallelism": f"replicas x{world}"},
+                   "l2": f"no flush: the {(8 << N_QUBITS) / 2**30:g} GiB state exceeds the 129 MB L2",
+                   "parallelism": f"replicas x{world}"},
         "gates_per_s": round(world * n_gates / (gates_ms * 1e-3), 1),
         "gate_time_ms_per_step": round(gates_ms, 3),
         "roofline": {"bound": "hbm", "kernel": "k_dense (1-qubit dense, SU(2))", "achieved": round(achieved, 1),

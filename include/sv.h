@@ -232,6 +232,13 @@ SV_API sv_status_t sv_norm2(sv_handle_t h, double *out);
  * up since the last call (SV_ERR_TIMEOUT), then clear the flag. */
 SV_API sv_status_t sv_check_device_status(sv_handle_t h);
 
+/* Diagnostic of device-side failure detection: launch one wait that nothing
+ * completes, bounded to `cycles` SM clock ticks (1e3..4e9), then report the
+ * device status as sv_check_device_status does. A working build returns
+ * SV_ERR_TIMEOUT (and clears the flag); the context stays usable. The
+ * tensor-core kernel bounds every one of its waits the same way. */
+SV_API sv_status_t sv_check_bounded_wait(sv_handle_t h, long long cycles);
+
 /* Number of kernels this handle has launched since sv_create. */
 SV_API sv_status_t sv_launch_count(sv_handle_t h, uint64_t *out);
 

@@ -94,11 +94,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
 }
 
 // Bounded wait: false on timeout or when another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag, int *d_err) {
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag, int *d_err,
+                                          long long budget = kWaitCycles) {
     const long long t0 = clock64();
     while (!mbar_try(a, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > budget) {
             *abort_flag = 1;
             atomicExch(d_err, kErrTimeout);
             return false;
@@ -483,6 +484,19 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// Diagnostic of the bounded wait: one thread waits on an mbarrier whose phase
+// never completes (nothing arrives), with a budget of `cycles` clock ticks, so
+// the wait must give up and record kErrTimeout in the status word.
+__global__ void k_wait_probe(int *d_err, long long cycles) {
+    __shared__ unsigned long long bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    abort_flag = 0;
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(smem_u32(&bar), 0, &abort_flag, d_err, cycles);
+}
+
 // ---------------- host: operand image of A ----------------
 uint32_t host_tf32(float x) {
     // round to nearest (ties away from zero) to a 10-bit mantissa, as cvt.rna.tf32.f32
@@ -584,6 +598,12 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
     if (prec == SV_PREC_TF32) return vec4 ? run_tc<TF32, true>(L, s, G, a, d_err) : run_tc<TF32, false>(L, s, G, a, d_err);
     return vec4 ? run_tc<BF16, true>(L, s, G, a, d_err) : run_tc<BF16, false>(L, s, G, a, d_err);
+}
+
+cudaError_t launch_wait_probe(const LaunchCtx &L, int *d_err, long long cycles) {
+    k_wait_probe<<<1, 32, 0, L.stream>>>(d_err, cycles);
+    ++*L.launches;
+    return cudaGetLastError();
 }
 
 }  // namespace svk

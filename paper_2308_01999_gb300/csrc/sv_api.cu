@@ -709,6 +709,13 @@ sv_status_t sv_check_device_status(sv_handle_t h) {
     return SV_ERR_TIMEOUT;
 }
 
+sv_status_t sv_check_bounded_wait(sv_handle_t h, long long cycles) {
+    if (!h || cycles < 1000 || cycles > 4000000000ll) return SV_ERR_INVALID_ARGUMENT;
+    DeviceGuard dg(h->device);
+    if (svk::launch_wait_probe(lctx(h), h->d_err, cycles) != cudaSuccess) return SV_ERR_CUDA;
+    return sv_check_device_status(h);
+}
+
 sv_status_t sv_launch_count(sv_handle_t h, uint64_t *out) {
     if (!h || !out) return SV_ERR_INVALID_ARGUMENT;
     *out = h->launches;

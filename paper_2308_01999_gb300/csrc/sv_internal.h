@@ -89,6 +89,8 @@ cudaError_t launch_set_basis(const LaunchCtx &L, sv_dtype_t dt, void *sv, int n,
 cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, const double *mat,
                        sv_precision_t prec, void *d_a, int *d_err);
 bool tc6_supported(int n, const int *tpos);
+// Bounded-wait diagnostic: a wait that nothing completes, limited to `cycles` clocks.
+cudaError_t launch_wait_probe(const LaunchCtx &L, int *d_err, long long cycles);
 
 // ---- batched small states (k_batch.cu, sv_batch.cu) ----
 // One persistent launch advances many independent states. Each state's gates

@@ -41,6 +41,7 @@ EXPORTED = [
     "sv_check_device_status", "sv_launch_count", "sv_status_string", "sv_expectation_pauli_noalloc",
     "sv_batch_create", "sv_batch_destroy", "sv_batch_compile", "sv_batch_info", "sv_batch_launch",
     "sv_batch_results", "sv_swap_index_bits", "sv_apply_pauli_rotation", "sv_sample",
+    "sv_check_bounded_wait",
 ]
 
 
@@ -91,6 +92,7 @@ def lib():
             "sv_swap_index_bits": [_VP, _I, C.c_int],
             "sv_apply_pauli_rotation": [_VP, C.c_double, _I, _I, C.c_int],
             "sv_sample": [_VP, _D, C.c_int, C.POINTER(C.c_int64)],
+            "sv_check_bounded_wait": [_VP, C.c_longlong],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -300,6 +302,11 @@ def sv_norm2(h: int) -> float:
 
 def sv_check_device_status(h: int) -> int:
     return int(lib().sv_check_device_status(_VP(h)))
+
+
+def sv_check_bounded_wait(h: int, cycles: int) -> int:
+    """Run the bounded-wait diagnostic; returns the status code (SV_ERR_TIMEOUT = 5 expected)."""
+    return int(lib().sv_check_bounded_wait(_VP(h), C.c_longlong(cycles)))
 
 
 def sv_launch_count(h: int) -> int:
