@@ -147,6 +147,23 @@ SV_API sv_status_t sv_apply_fused(sv_handle_t h, const sv_gate_t *gates, int n_g
  * n_pairs outside 1..18. */
 SV_API sv_status_t sv_swap_index_bits(sv_handle_t h, const int *bit_pairs, int n_pairs);
 
+/* Fusion options: max_fused_qubits as above (1..6); max_fused_diagonal_qubits
+ * (0 = off, else 1..6) sends diagonal gates (CZ, CRZ, phases, controlled
+ * diagonals) to separate diagonal blocks of up to that many qubits, applied by
+ * the diagonal kernel (Sec. II-D-1: dense/diagonal fusion with
+ * max_fused_gate_size and max_fused_diagonal_gate_size); precision as above. */
+typedef struct {
+    int max_fused_qubits;
+    int max_fused_diagonal_qubits;
+    sv_precision_t precision;
+} sv_fusion_options_t;
+
+/* sv_apply_fused with explicit options (sv_apply_fused is this call with
+ * max_fused_diagonal_qubits = 0). Errors as sv_apply_fused, and
+ * INVALID_ARGUMENT for an option out of range or a NULL opt. */
+SV_API sv_status_t sv_apply_fused_ex(sv_handle_t h, const sv_gate_t *gates, int n_gates,
+                                     const sv_fusion_options_t *opt, int *n_fused_out);
+
 /* Host-only view of the fusion pass, for inspection and tests (no GPU needed).
  * Writes at most max_blocks blocks: block b acts on block_k[b] qubits
  * block_targets[6*b .. 6*b+k-1] (bit j of its matrix index is target j) with
@@ -156,6 +173,11 @@ SV_API sv_status_t sv_swap_index_bits(sv_handle_t h, const int *bit_pairs, int n
 SV_API sv_status_t sv_fuse_plan(const sv_gate_t *gates, int n_gates, int n_qubits, int max_fused_qubits,
                          int max_blocks, int *n_blocks_out, int *block_k, int *block_targets,
                          double *block_matrices);
+
+/* sv_fuse_plan with explicit fusion options (the precision field is ignored). */
+SV_API sv_status_t sv_fuse_plan_ex(const sv_gate_t *gates, int n_gates, int n_qubits, const sv_fusion_options_t *opt,
+                                   int max_blocks, int *n_blocks_out, int *block_k, int *block_targets,
+                                   double *block_matrices);
 
 /* Pauli-string expectation values (Table I, "Expectation"):
  * out[s] = Re <psi| P_s |psi>, P_s = prod_i paulis[s*n_sites + i] on qubit

@@ -213,12 +213,23 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
             double acc = 0.0;
             float run = 0.f;
             int cnt = 0;
-            for (uint32_t i = threadIdx.x; i < N; i += kT) {
+            // terms i and i ^ x come from the same pair of loads: w_i = psi_i conj(psi_{i^x}),
+            // w_{i^x} = conj(w_i); pairs are enumerated by clearing the lowest bit of x
+            const int pb = x ? __ffs(x) - 1 : 0;
+            const uint32_t npairs = x ? N / 2 : N;
+            for (uint32_t g = threadIdx.x; g < npairs; g += kT) {
+                const uint32_t i = x ? (((g >> pb) << (pb + 1)) | (g & ((1u << pb) - 1u))) : g;
+                const uint32_t j = i ^ x;
                 const float2 a = n == T ? tile[i] : sv[i];
-                const float2 b = n == T ? tile[i ^ x] : sv[i ^ x];
-                const float t = P.use_im ? (a.y * b.x - a.x * b.y) : (a.x * b.x + a.y * b.y);
-                run += (__popc(i & z) & 1) ? -t : t;
-                if (++cnt == 16) {
+                const float2 b = x ? (n == T ? tile[j] : sv[j]) : a;
+                const float re = a.x * b.x + a.y * b.y, im = a.y * b.x - a.x * b.y;
+                const float ti = P.use_im ? im : re;
+                run += (__popc(i & z) & 1) ? -ti : ti;
+                if (x) {
+                    const float tj = P.use_im ? -im : re;
+                    run += (__popc(j & z) & 1) ? -tj : tj;
+                }
+                if (++cnt == 8) {
                     acc += (double)run;
                     run = 0.f;
                     cnt = 0;

@@ -418,8 +418,17 @@ sv_status_t sv_swap_index_bits(sv_handle_t h, const int *bit_pairs, int n_pairs)
 
 sv_status_t sv_fuse_plan(const sv_gate_t *gates, int n_gates, int n_qubits, int max_fused_qubits, int max_blocks,
                          int *n_blocks_out, int *block_k, int *block_targets, double *block_matrices) {
-    if ((!gates && n_gates > 0) || n_gates < 0 || !n_blocks_out || n_qubits < 1 || n_qubits > SV_MAX_QUBITS)
+    sv_fusion_options_t opt{max_fused_qubits, 0, SV_PREC_NATIVE};
+    return sv_fuse_plan_ex(gates, n_gates, n_qubits, &opt, max_blocks, n_blocks_out, block_k, block_targets,
+                           block_matrices);
+}
+
+sv_status_t sv_fuse_plan_ex(const sv_gate_t *gates, int n_gates, int n_qubits, const sv_fusion_options_t *opt,
+                            int max_blocks, int *n_blocks_out, int *block_k, int *block_targets,
+                            double *block_matrices) {
+    if ((!gates && n_gates > 0) || n_gates < 0 || !n_blocks_out || !opt || n_qubits < 1 || n_qubits > SV_MAX_QUBITS)
         return SV_ERR_INVALID_ARGUMENT;
+    const int max_fused_qubits = opt->max_fused_qubits;
     for (int i = 0; i < n_gates; ++i) {
         const sv_gate_t &g = gates[i];
         if (g.n_targets < 1 || g.n_targets > SV_MAX_TARGETS || g.n_controls < 0 || g.n_controls > SV_MAX_CONTROLS ||
@@ -428,7 +437,7 @@ sv_status_t sv_fuse_plan(const sv_gate_t *gates, int n_gates, int n_qubits, int 
             return SV_ERR_INVALID_ARGUMENT;
     }
     std::vector<svf::Item> items;
-    sv_status_t s = svf::fuse(gates, n_gates, n_qubits, max_fused_qubits, items);
+    sv_status_t s = svf::fuse(gates, n_gates, n_qubits, max_fused_qubits, items, opt->max_fused_diagonal_qubits);
     if (s != SV_OK) return s;
     *n_blocks_out = (int)items.size();
     if ((int)items.size() > max_blocks) return SV_ERR_INSUFFICIENT_WORKSPACE;
@@ -481,7 +490,17 @@ sv_status_t sv_fuse_plan(const sv_gate_t *gates, int n_gates, int n_qubits, int 
 
 sv_status_t sv_apply_fused(sv_handle_t h, const sv_gate_t *gates, int n_gates, int max_fused_qubits,
                            sv_precision_t prec, int *n_fused_out) {
-    if (!h || (!gates && n_gates > 0) || n_gates < 0 || max_fused_qubits < 1 || max_fused_qubits > SV_MAX_TARGETS ||
+    sv_fusion_options_t opt{max_fused_qubits, 0, prec};
+    return sv_apply_fused_ex(h, gates, n_gates, &opt, n_fused_out);
+}
+
+sv_status_t sv_apply_fused_ex(sv_handle_t h, const sv_gate_t *gates, int n_gates, const sv_fusion_options_t *opt,
+                              int *n_fused_out) {
+    if (!h || !opt || (!gates && n_gates > 0) || n_gates < 0) return SV_ERR_INVALID_ARGUMENT;
+    const int max_fused_qubits = opt->max_fused_qubits;
+    const sv_precision_t prec = opt->precision;
+    if (max_fused_qubits < 1 || max_fused_qubits > SV_MAX_TARGETS || opt->max_fused_diagonal_qubits < 0 ||
+        opt->max_fused_diagonal_qubits > SV_MAX_TARGETS ||
         (prec != SV_PREC_NATIVE && prec != SV_PREC_TF32 && prec != SV_PREC_SPLIT_BF16))
         return SV_ERR_INVALID_ARGUMENT;
     if (prec != SV_PREC_NATIVE && h->dt != SV_C64) return SV_ERR_NOT_SUPPORTED;
@@ -492,7 +511,7 @@ sv_status_t sv_apply_fused(sv_handle_t h, const sv_gate_t *gates, int n_gates, i
         if (s != SV_OK) return s;
     }
     std::vector<svf::Item> items;
-    sv_status_t s = svf::fuse(gates, n_gates, h->n, max_fused_qubits, items);
+    sv_status_t s = svf::fuse(gates, n_gates, h->n, max_fused_qubits, items, opt->max_fused_diagonal_qubits);
     if (s != SV_OK) return s;
     DeviceGuard dg(h->device);
     std::vector<int> pairs, map;

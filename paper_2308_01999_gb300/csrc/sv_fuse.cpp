@@ -95,20 +95,66 @@ void absorb(Item &b, const sv_gate_t &g) {
 
 }  // namespace
 
-sv_status_t fuse(const sv_gate_t *gates, int n_gates, int n_qubits, int width, std::vector<Item> &out) {
+bool gate_is_diagonal(const sv_gate_t &g) {
+    const int D = 1 << g.n_targets;
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c)
+            if (r != c && (g.matrix[2 * (r * D + c)] != 0.0 || g.matrix[2 * (r * D + c) + 1] != 0.0)) return false;
+    return true;
+}
+
+sv_status_t fuse(const sv_gate_t *gates, int n_gates, int n_qubits, int width, std::vector<Item> &out,
+                 int diag_width) {
     out.clear();
-    if (width < 1 || width > SV_MAX_TARGETS || n_qubits < 1 || n_qubits > SV_MAX_QUBITS || n_gates < 0)
+    if (width < 1 || width > SV_MAX_TARGETS || n_qubits < 1 || n_qubits > SV_MAX_QUBITS || n_gates < 0 ||
+        diag_width < 0 || diag_width > SV_MAX_TARGETS)
         return SV_ERR_INVALID_ARGUMENT;
-    std::vector<int> last(n_qubits, -1);   // latest item touching each qubit
-    constexpr int kScan = 64;              // blocks examined per gate
+    std::vector<int> last(n_qubits, -1);      // latest item touching each qubit
+    std::vector<int> last_nd(n_qubits, -1);   // latest non-diagonal item touching each qubit
+    constexpr int kScan = 64;                 // blocks examined per gate
+    auto new_block = [&](const std::vector<int> &Q, bool diag) {
+        Item it;
+        it.qubits = Q;
+        it.diagonal = diag;
+        const uint64_t d = 1ull << Q.size();
+        it.m.assign(d * d, cd(0));
+        for (uint64_t i = 0; i < d; ++i) it.m[i * d + i] = 1;
+        out.push_back(std::move(it));
+        return (int)out.size() - 1;
+    };
+    auto growth_of = [&](const Item &b, const std::vector<int> &Q) {
+        int g = 0;
+        for (int q : Q)
+            if (local_index(b.qubits, q) < 0) ++g;
+        return g;
+    };
     for (int gi = 0; gi < n_gates; ++gi) {
         const sv_gate_t &g = gates[gi];
         const int nq = g.n_targets + g.n_controls;
-        int L = -1;
+        int L = -1, Lnd = -1;
         std::vector<int> Q(nq);
         for (int t = 0; t < nq; ++t) {
             Q[t] = t < g.n_targets ? g.targets[t] : g.controls[t - g.n_targets];
             L = std::max(L, last[Q[t]]);
+            Lnd = std::max(Lnd, last_nd[Q[t]]);
+        }
+        if (diag_width > 0 && nq <= diag_width && gate_is_diagonal(g)) {
+            // diagonal blocks after the last non-diagonal item on these qubits
+            int best = -1, best_growth = 1 << 30;
+            const int lo = std::max({Lnd + 1, 0, (int)out.size() - kScan});
+            for (int j = (int)out.size() - 1; j >= lo; --j) {
+                const Item &b = out[j];
+                if (!b.diagonal) continue;
+                const int gr = growth_of(b, Q);
+                if ((int)b.qubits.size() + gr <= diag_width && gr < best_growth) {
+                    best = j;
+                    best_growth = gr;
+                }
+            }
+            if (best < 0) best = new_block(Q, true);
+            absorb(out[best], g);
+            for (int q : Q) last[q] = std::max(last[q], best);
+            continue;
         }
         if (nq > width) {
             Item it;
@@ -116,33 +162,23 @@ sv_status_t fuse(const sv_gate_t *gates, int n_gates, int n_qubits, int width, s
             it.gate = gi;
             it.n_gates = 1;
             out.push_back(std::move(it));
-            for (int q : Q) last[q] = (int)out.size() - 1;
+            for (int q : Q) last[q] = last_nd[q] = (int)out.size() - 1;
             continue;
         }
         int best = -1, best_growth = 1 << 30;
         const int lo = std::max({L, 0, (int)out.size() - kScan});
         for (int j = (int)out.size() - 1; j >= lo; --j) {
             const Item &b = out[j];
-            if (b.passthrough) continue;
-            int growth = 0;
-            for (int q : Q)
-                if (local_index(b.qubits, q) < 0) ++growth;
-            if ((int)b.qubits.size() + growth <= width && growth < best_growth) {
+            if (b.passthrough || b.diagonal) continue;
+            const int gr = growth_of(b, Q);
+            if ((int)b.qubits.size() + gr <= width && gr < best_growth) {
                 best = j;
-                best_growth = growth;
+                best_growth = gr;
             }
         }
-        if (best < 0) {
-            Item it;
-            it.qubits = Q;
-            const uint64_t d = 1ull << nq;
-            it.m.assign(d * d, cd(0));
-            for (uint64_t i = 0; i < d; ++i) it.m[i * d + i] = 1;
-            out.push_back(std::move(it));
-            best = (int)out.size() - 1;
-        }
+        if (best < 0) best = new_block(Q, false);
         absorb(out[best], g);
-        for (int q : Q) last[q] = best;
+        for (int q : Q) last[q] = last_nd[q] = best;
     }
     return SV_OK;
 }

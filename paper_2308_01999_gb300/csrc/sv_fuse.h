@@ -19,6 +19,7 @@ struct Item {
     std::vector<int> qubits;     // fused block qubits
     std::vector<cd> m;           // 2^k x 2^k row-major, k = qubits.size()
     int n_gates = 0;             // gates absorbed
+    bool diagonal = false;       // a block of diagonal gates only (its matrix is diagonal)
 };
 
 // Greedy fusion in program order. A gate joins the open block that needs the
@@ -26,7 +27,14 @@ struct Item {
 // of its qubits (so it only moves past blocks on disjoint qubits, with which it
 // commutes), provided the block stays within `width` qubits; otherwise it opens
 // a new block. Block matrices are composed in FP64.
-sv_status_t fuse(const sv_gate_t *gates, int n_gates, int n_qubits, int width, std::vector<Item> &out);
+//
+// With diag_width > 0, diagonal gates (Sec. II-D-1, dense/diagonal fusion) go
+// to separate diagonal blocks of at most diag_width qubits instead: since
+// diagonal matrices commute, such a gate may join any diagonal block after the
+// last non-diagonal item touching its qubits. Dense blocks then take only the
+// other gates.
+sv_status_t fuse(const sv_gate_t *gates, int n_gates, int n_qubits, int width, std::vector<Item> &out,
+                 int diag_width = 0);
 
 // psi <- G psi for a (controlled) k-qubit gate on an s-qubit vector (host, FP64);
 // used to compose block matrices column by column.

@@ -33,7 +33,7 @@ __all__ = [
     "dense_form", "random_state", "random_pauli_strings", "layered_random_circuit",
     "circuit_config0", "circuit_config1", "circuit_config2", "ansatz_circuit",
     "batched_ansatz_workload", "ghz_circuit", "qft_circuit", "random_gate_dense",
-    "serving_trace", "PAULI_I", "PAULI_X", "PAULI_Y", "PAULI_Z",
+    "serving_trace", "gate_rx", "gate_zz", "qaoa_circuit", "PAULI_I", "PAULI_X", "PAULI_Y", "PAULI_Z",
 ]
 
 PAULI_I, PAULI_X, PAULI_Y, PAULI_Z = 0, 1, 2, 3
@@ -284,6 +284,38 @@ def batched_ansatz_workload(count: int = 4096, nmin: int = 10, nmax: int = 20,
         paulis, sites = random_pauli_strings(n, strings, rng)
         out.append((n, gates, paulis, sites))
     return out
+
+
+def gate_rx(theta: float) -> np.ndarray:
+    """RX(theta) = [[cos theta/2, -i sin theta/2], [-i sin theta/2, cos theta/2]]."""
+    c, s = np.cos(0.5 * theta), np.sin(0.5 * theta)
+    return np.array([[c, -1j * s], [-1j * s, c]], dtype=np.complex128)
+
+
+def gate_zz(theta: float) -> np.ndarray:
+    """exp(-i theta/2 Z(x)Z) on two targets: diag(e^{-i t/2}, e^{i t/2}, e^{i t/2}, e^{-i t/2})."""
+    a, b = np.exp(-0.5j * theta), np.exp(0.5j * theta)
+    return np.diag([a, b, b, a]).astype(np.complex128)
+
+
+def qaoa_circuit(n: int, p: int, seed: int, edges_per_qubit: int = 3) -> list:
+    """QAOA-style circuit on a random graph: H on every qubit, then p rounds of
+    ZZ(gamma) on each edge (diagonal two-qubit gates) and RX(beta) on every
+    qubit; angles uniform on [0, 2 pi)."""
+    rng = rng_for(seed)
+    edges = set()
+    while len(edges) < (n * edges_per_qubit) // 2:
+        a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+        edges.add((min(a, b), max(a, b)))
+    edges = sorted(edges)
+    gates = [Gate((q,), gate_h(), (), (), "h") for q in range(n)]
+    for _ in range(p):
+        gamma, beta = rng.uniform(0, 2 * np.pi, size=2)
+        for a, b in edges:
+            gates.append(Gate((a, b), gate_zz(float(gamma)), (), (), "zz"))
+        for q in range(n):
+            gates.append(Gate((q,), gate_rx(float(beta)), (), (), "rx"))
+    return gates
 
 
 def ghz_circuit(n: int) -> list:

@@ -41,7 +41,7 @@ EXPORTED = [
     "sv_check_device_status", "sv_launch_count", "sv_status_string", "sv_expectation_pauli_noalloc",
     "sv_batch_create", "sv_batch_destroy", "sv_batch_compile", "sv_batch_info", "sv_batch_launch",
     "sv_batch_results", "sv_swap_index_bits", "sv_apply_pauli_rotation", "sv_sample",
-    "sv_check_bounded_wait",
+    "sv_check_bounded_wait", "sv_apply_fused_ex", "sv_fuse_plan_ex",
 ]
 
 
@@ -49,6 +49,10 @@ class SvError(RuntimeError):
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {STATUS.get(code, code)}")
         self.code = code
+
+
+class sv_fusion_options_t(C.Structure):
+    _fields_ = [("max_fused_qubits", C.c_int), ("max_fused_diagonal_qubits", C.c_int), ("precision", C.c_int)]
 
 
 class sv_gate_t(C.Structure):
@@ -93,6 +97,9 @@ def lib():
             "sv_apply_pauli_rotation": [_VP, C.c_double, _I, _I, C.c_int],
             "sv_sample": [_VP, _D, C.c_int, C.POINTER(C.c_int64)],
             "sv_check_bounded_wait": [_VP, C.c_longlong],
+            "sv_apply_fused_ex": [_VP, C.POINTER(sv_gate_t), C.c_int, C.POINTER(sv_fusion_options_t), _I],
+            "sv_fuse_plan_ex": [C.POINTER(sv_gate_t), C.c_int, C.c_int, C.POINTER(sv_fusion_options_t), C.c_int, _I,
+                                _I, _I, _D],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -198,7 +205,18 @@ def sv_apply_fused(h: int, gates, max_fused_qubits: int, prec: int = SV_PREC_NAT
     return nf.value
 
 
-def sv_fuse_plan(gates, n_qubits: int, max_fused_qubits: int, max_blocks: int | None = None):
+def sv_apply_fused_ex(h: int, gates, max_fused_qubits: int, max_fused_diagonal_qubits: int = 0,
+                      prec: int = SV_PREC_NATIVE) -> int:
+    """sv_apply_fused with a separate width for diagonal blocks; returns the block count."""
+    arr, _keep = _gate_array(gates)
+    opt = sv_fusion_options_t(int(max_fused_qubits), int(max_fused_diagonal_qubits), int(prec))
+    nf = C.c_int(0)
+    _check(lib().sv_apply_fused_ex(_VP(h), arr, len(gates), C.byref(opt), C.byref(nf)), "sv_apply_fused_ex")
+    return nf.value
+
+
+def sv_fuse_plan(gates, n_qubits: int, max_fused_qubits: int, max_blocks: int | None = None,
+                 max_fused_diagonal_qubits: int = 0):
     """Host-only fusion plan: list of (targets tuple, matrix) in application order."""
     arr, _keep = _gate_array(gates)
     cap = max_blocks if max_blocks is not None else max(1, len(gates))
@@ -206,9 +224,10 @@ def sv_fuse_plan(gates, n_qubits: int, max_fused_qubits: int, max_blocks: int | 
     ks = np.zeros(cap, dtype=np.int32)
     ts = np.zeros(cap * SV_MAX_TARGETS, dtype=np.int32)
     ms = np.zeros(cap * 64 * 64 * 2, dtype=np.float64)
-    _check(lib().sv_fuse_plan(arr, len(gates), int(n_qubits), int(max_fused_qubits), cap, C.byref(nb),
-                              ks.ctypes.data_as(_I), ts.ctypes.data_as(_I), ms.ctypes.data_as(_D)),
-           "sv_fuse_plan")
+    opt = sv_fusion_options_t(int(max_fused_qubits), int(max_fused_diagonal_qubits), SV_PREC_NATIVE)
+    _check(lib().sv_fuse_plan_ex(arr, len(gates), int(n_qubits), C.byref(opt), cap, C.byref(nb),
+                                 ks.ctypes.data_as(_I), ts.ctypes.data_as(_I), ms.ctypes.data_as(_D)),
+           "sv_fuse_plan_ex")
     out = []
     for b in range(nb.value):
         k = int(ks[b])
@@ -367,7 +386,10 @@ class StateVector:
         for g in gates:
             self.apply_gate(g)
 
-    def apply_fused(self, gates, max_fused_qubits: int, prec: int = SV_PREC_NATIVE) -> int:
+    def apply_fused(self, gates, max_fused_qubits: int, prec: int = SV_PREC_NATIVE,
+                    max_fused_diagonal_qubits: int = 0) -> int:
+        if max_fused_diagonal_qubits:
+            return sv_apply_fused_ex(self.handle, gates, max_fused_qubits, max_fused_diagonal_qubits, prec)
         return sv_apply_fused(self.handle, gates, max_fused_qubits, prec)
 
     def expectation_pauli(self, paulis, sites):

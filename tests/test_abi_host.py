@@ -85,3 +85,16 @@ def test_fusion_rejects_bad_gates(sv):
         sv.sv_fuse_plan([gen.Gate((3,), np.eye(2))], 3, 2)
     with pytest.raises(sv.SvError):
         sv.sv_fuse_plan([gen.Gate((0,), np.eye(2))], 3, 7)
+
+
+@pytest.mark.parametrize("width,dwidth", [(2, 4), (3, 6), (4, 5), (6, 6)])
+def test_diagonal_fusion_plan_reproduces_circuit(sv, width, dwidth):
+    n = 10
+    gates = gen.qaoa_circuit(n, 2, seed=width + dwidth)
+    ref = orc.run_circuit(gates, n)
+    plan = sv.sv_fuse_plan(gates, n, width, max_fused_diagonal_qubits=dwidth)
+    plain = sv.sv_fuse_plan(gates, n, width)
+    np.testing.assert_allclose(_apply_plan(plan, n), ref, atol=1e-12, rtol=0)
+    diag = [m for _, m in plan if np.count_nonzero(m - np.diag(np.diag(m))) == 0 and m.shape[0] > 2]
+    assert diag and max(m.shape[0] for m in diag) <= (1 << dwidth)
+    assert max(len(t) for t, _ in plain) <= width

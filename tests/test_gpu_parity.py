@@ -336,3 +336,17 @@ def test_z_expectations_of_every_qubit_in_one_pass(env, name, n):
     got = s.expectation_pauli(paulis, sites)
     want = [orc.expect_pauli(ref, p, q).real for p, q in zip(paulis, sites)]
     assert_exp(got, want, name, "mixed single-Z strings")
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("width,dwidth", [(2, 4), (3, 6), (4, 6)])
+def test_dense_and_diagonal_fusion(env, name, width, dwidth):
+    """Diagonal gates fused into diagonal blocks of up to dwidth qubits, the
+    rest into dense blocks of up to width qubits (QAOA-style circuit)."""
+    n = 13
+    gates = gen.qaoa_circuit(n, 3, seed=width * 10 + dwidth)
+    ref = orc.run_circuit(gates, n)
+    psi, s = make_state(env, n, name)
+    nf = s.apply_fused(gates, width, max_fused_diagonal_qubits=dwidth)
+    assert nf < len(gates)
+    assert_amps(host(psi), ref, name, f"fused w={width} diag={dwidth}")
