@@ -52,10 +52,16 @@ __device__ __forceinline__ uint32_t member_off(int j, const BOp &op) {
 template <int K>
 __device__ void op_dense(float2 *tile, const BOp &op, const float2 *msh, int T) {
     constexpr int D = 1 << K;
+    constexpr bool kRegMat = K <= 2;      // small matrices live in registers
     const int ngroups = 1 << (T - op.np);
     uint32_t off[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) off[j] = member_off<K>(j, op);
+    float2 mreg[kRegMat ? D * D : 1];
+    if constexpr (kRegMat) {
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) mreg[i] = msh[i];
+    }
     for (int g = threadIdx.x; g < ngroups; g += kT) {
         const uint32_t base = insert_zeros_local((uint32_t)g, op);
         float2 v[D];
@@ -66,7 +72,7 @@ __device__ void op_dense(float2 *tile, const BOp &op, const float2 *msh, int T) 
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int l = 0; l < D; ++l) {
-                const float2 m = msh[j * D + l];
+                const float2 m = kRegMat ? mreg[j * D + l] : msh[j * D + l];
                 acc.x = __fmaf_rn(m.x, v[l].x, acc.x);
                 acc.x = __fmaf_rn(-m.y, v[l].y, acc.x);
                 acc.y = __fmaf_rn(m.x, v[l].y, acc.y);
@@ -126,8 +132,9 @@ __global__ void __launch_bounds__(kT, 1)
 k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_items, const BStage *__restrict__ stages,
         const BOp *__restrict__ ops, const float2 *__restrict__ pool, const BStr *__restrict__ strs,
         double *__restrict__ out, int *__restrict__ counter, int keep_states) {
-    extern __shared__ float2 tile[];                 // 2^kBatchTileQubits amplitudes
-    __shared__ float2 msh[2 * 256];                  // current op's matrix / table
+    extern __shared__ float2 tile[];                 // 2^kBatchTileQubits amplitudes, then the stage's matrices
+    float2 *smat = tile + (1 << kBatchTileQubits);   // kBatchStageMat entries
+    __shared__ float2 msh[2 * 256];                  // one op's matrix when the stage's do not fit
     __shared__ uint32_t lo_tab[128], hi_tab[128];    // local bits 0..6 / 7..13 -> amplitude bits
     __shared__ double red[kT / 32];
     __shared__ int s_item;
@@ -156,6 +163,10 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
                 (hi ? hi_tab : lo_tab)[v] = a;
             }
             const uint32_t other = (uint32_t)(~S.lmask & ((1ull << n) - 1ull));
+            // the stage's matrices stay in shared memory for all of its tiles
+            const bool staged = S.pool_count <= kBatchStageMat;
+            if (staged)
+                for (int i = threadIdx.x; i < S.pool_count; i += kT) smat[i] = pool[S.pool_begin + i];
             __syncthreads();
             for (uint32_t ti = 0; ti < ntiles; ++ti) {
                 uint32_t tbase = 0;
@@ -176,27 +187,34 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
                 }
                 for (int o = S.op_begin; o < S.op_end; ++o) {
                     const BOp op = ops[o];
-                    const int D = 1 << op.k;
-                    const int nm = op.kind == BOP_DENSE ? D * D : (op.kind == BOP_PERM ? 2 * D : D);
-                    __syncthreads();   // previous op done with the tile and msh
-                    for (int i = threadIdx.x; i < nm; i += kT) msh[i] = pool[op.mat + i];
-                    __syncthreads();
+                    const float2 *m;
+                    if (staged) {
+                        m = smat + (op.mat - S.pool_begin);
+                        __syncthreads();   // the previous op is done with the tile
+                    } else {
+                        const int D = 1 << op.k;
+                        const int nm = op.kind == BOP_DENSE ? D * D : (op.kind == BOP_PERM ? 2 * D : D);
+                        __syncthreads();   // previous op done with the tile and msh
+                        for (int i = threadIdx.x; i < nm; i += kT) msh[i] = pool[op.mat + i];
+                        __syncthreads();
+                        m = msh;
+                    }
                     if (op.kind == BOP_DENSE) {
                         switch (op.k) {
-                        case 1: op_dense<1>(tile, op, msh, T); break;
-                        case 2: op_dense<2>(tile, op, msh, T); break;
-                        case 3: op_dense<3>(tile, op, msh, T); break;
-                        default: op_dense<4>(tile, op, msh, T); break;
+                        case 1: op_dense<1>(tile, op, m, T); break;
+                        case 2: op_dense<2>(tile, op, m, T); break;
+                        case 3: op_dense<3>(tile, op, m, T); break;
+                        default: op_dense<4>(tile, op, m, T); break;
                         }
                     } else if (op.kind == BOP_PERM) {
                         switch (op.k) {
-                        case 1: op_perm<1>(tile, op, msh, T); break;
-                        case 2: op_perm<2>(tile, op, msh, T); break;
-                        case 3: op_perm<3>(tile, op, msh, T); break;
-                        default: op_perm<4>(tile, op, msh, T); break;
+                        case 1: op_perm<1>(tile, op, m, T); break;
+                        case 2: op_perm<2>(tile, op, m, T); break;
+                        case 3: op_perm<3>(tile, op, m, T); break;
+                        default: op_perm<4>(tile, op, m, T); break;
                         }
                     } else {
-                        op_diag(tile, op, msh, T);
+                        op_diag(tile, op, m, T);
                     }
                 }
                 __syncthreads();
@@ -247,7 +265,7 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
 cudaError_t launch_batch(const LaunchCtx &L, float2 *states, const BItem *items, int n_items, const BStage *stages,
                          const BOp *ops, const float2 *pool, const BStr *strs, double *out, int *counter,
                          int keep_states) {
-    const int smem = (int)sizeof(float2) << kBatchTileQubits;
+    const int smem = (int)sizeof(float2) * ((1 << kBatchTileQubits) + kBatchStageMat);
     cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(counter, 0, sizeof(int), L.stream);

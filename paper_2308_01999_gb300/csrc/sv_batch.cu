@@ -261,6 +261,8 @@ SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, 
                 b->ops.push_back(op);
             }
             bs.op_end = (int)b->ops.size();
+            bs.pool_begin = bs.op_end > bs.op_begin ? (int)b->ops[bs.op_begin].mat : (int)b->pool.size();
+            bs.pool_count = (int)b->pool.size() - bs.pool_begin;
             b->stages.push_back(bs);
         }
         bi.stage_end = (int)b->stages.size();

@@ -114,7 +114,9 @@ struct BItem {
 struct BStage {
     uint64_t lmask;          // the T local qubits
     int op_begin, op_end;
+    int pool_begin, pool_count;   // the stage's matrices: pool[pool_begin .. pool_begin + pool_count)
 };
+constexpr int kBatchStageMat = 4096;   // float2 entries of one stage staged in shared memory at once
 
 struct BOp {
     uint8_t kind, k, np, nt;  // kind, targets, inserted positions, (unused)
