@@ -53,6 +53,8 @@ constexpr int kEpi = kEpiWarps * 32;
 constexpr int kAImg = 64 * 1024;      // bytes of the A image (either precision)
 constexpr int kBStage = 64 * 1024;    // bytes of one B tile (either precision)
 constexpr int kTmemCols = 2 * kNT;    // two accumulators
+constexpr int kStgPitch = 17;         // floats per staged accumulator row (16 columns + 1 against bank conflicts)
+constexpr int kEpiStage = kEpiWarps * 32 * kStgPitch * 4;   // bytes of epilogue staging
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 constexpr int kErrTimeout = 0x7c01;
 
@@ -169,6 +171,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -206,7 +221,12 @@ __device__ __forceinline__ uint32_t sw128(int kb, int r, int chunk) {
     return (uint32_t)(kb * (kNT * 128) + (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4));
 }
 
-template <int P, bool VEC4>
+// PROD_COLS: producers load lane-per-column (lowest target >= 4), else in address order.
+// EPI: EPI_DIRECT stores 16-byte column pairs straight from the accumulator rows
+// (qubit 0 free, the rows a warp writes within a few MiB); EPI_COLS / EPI_MEMBERS
+// stage through shared memory and store runs of columns / of members.
+enum { EPI_DIRECT = 0, EPI_COLS = 1, EPI_MEMBERS = 2 };
+template <int P, bool PROD_COLS, int EPI>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *__restrict__ d_err) {
     extern __shared__ unsigned char smem_dyn[];
@@ -274,8 +294,8 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
 
     if (warp < kProdWarps) {
         // ---------------- producers ----------------
-        if constexpr (VEC4) {
-            // qubit 0 is not a target: lane n takes column n (8-byte loads, consecutive
+        if constexpr (PROD_COLS) {
+            // the lowest target is at least 4: lane n takes column n (8-byte loads, consecutive
             // lanes on consecutive columns, 32 loads in flight per thread) and stores
             // whole 16-byte chunks of the swizzled operand, free of bank conflicts
             const int n = threadIdx.x & (kNT - 1);          // column within the tile
@@ -407,71 +427,74 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
         __syncwarp();
     } else {
         // ---------------- epilogue ----------------
-        const int sub = warp & 3;                   // TMEM lanes 32*sub .. 32*sub+31
-        const int half = (warp - kProdWarps) >> 2;  // columns 64*half .. 64*half+63 of the tile
-        const int m = sub * 32 + lane;              // accumulator row = 2j + e
-        const int j = m >> 1, e = m & 1;
-        const uint64_t offj = G.off[j];
+        // Each warp reads 16 accumulator columns of its 32 TMEM lanes (16 members
+        // x re/im) at a time, stages them in shared memory, and stores them back
+        // so that every store instruction writes contiguous runs: 16 consecutive
+        // columns of one member row (qubit 0 free) or 16 consecutive members of
+        // one column (qubit 0 a target). Lane-per-row stores that scatter over 16
+        // rows run at a fraction of HBM bandwidth when the rows are far apart.
+        const int ew = warp - kProdWarps;
+        const int sub = warp & 3;                   // TMEM lanes 32*sub .. 32*sub+31: members 16*sub .. +15
+        const int half = ew >> 2;                   // columns 64*half .. 64*half+63 of the tile
+        float *stg = reinterpret_cast<float *>(sB0 + 2 * kBStage) + ew * 32 * kStgPitch;
+        uint64_t offr[8];                           // member offsets this lane stores
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int jj = EPI == EPI_COLS ? 2 * r + (lane >> 4) : (lane & 15);
+            offr[r] = G.off[16 * sub + jj];
+        }
         int i = 0;
         for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
             const int a = i & 1, u = i >> 1;
             if (!mbar_wait(smem_u32(&S.acc_full[a]), u & 1, abort_flag, d_err)) break;
             tc_fence_after();
-            const uint64_t tb = col_base(t * kNT, G) + offj;
-            const uint64_t tb2 = col_base(t * kNT, G) + G.off[(m >> 2) << 1];   // member 2p of this lane quad
+            const uint64_t tb = col_base(t * kNT, G);
             const uint64_t tcol = t * kNT;
+            if constexpr (EPI == EPI_DIRECT) {
+                // row m = 2j + e of this lane: the even lane stores columns (c, c+1) of
+                // member j, the odd lane (c+2, c+3), after one exchange of halves
+                const int e = lane & 1;
+                const uint64_t tbj = tb + G.off[16 * sub + (lane >> 1)];
 #pragma unroll 1
-            for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * kNT + cc * 32), v);
-                if constexpr (VEC4) {
-                    // qubit 0 is not a target, so columns c and c+1 (c even) are adjacent
-                    // amplitudes: the even lane stores (c, c+1), the odd lane (c+2, c+3)
+                for (int cc = 0; cc < 2; ++cc) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * kNT + half * 64 + cc * 32), v);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const float s0 = e ? v[4 * q] : v[4 * q + 2];
                         const float s1 = e ? v[4 * q + 1] : v[4 * q + 3];
                         const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1);
                         const float r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-                        const int ci = cc * 32 + 4 * q + (e ? 2 : 0);
+                        const int ci = half * 64 + cc * 32 + 4 * q + (e ? 2 : 0);
                         if (tcol + ci < G.n_cols) {
                             const float4 o = e ? make_float4(r0, v[4 * q + 2], r1, v[4 * q + 3])
                                                : make_float4(v[4 * q], r0, v[4 * q + 1], r1);
-                            *reinterpret_cast<float4 *>(sv + (tb | S.pd[ci])) = o;
+                            *reinterpret_cast<float4 *>(sv + (tbj | S.pd[ci])) = o;
                         }
-                    }
-                } else {
-                    // qubit 0 is the lowest target: members 2p and 2p+1 of a column are
-                    // adjacent amplitudes, held by lanes 4p..4p+3 as (re, im, re, im)
-                    // rows. A 4x4 transpose within each lane quad (three rotations)
-                    // gives lane 4p+r column c+r's 16 bytes.
-                    const int r4 = lane & 3, qbase = lane & ~3;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float own = r4 == 0 ? v[4 * q] : r4 == 1 ? v[4 * q + 1] : r4 == 2 ? v[4 * q + 2] : v[4 * q + 3];
-                        float t0v = own, t1v = 0.f, t2v = 0.f, t3v = 0.f;   // t_k = M[k][r4]
-#pragma unroll
-                        for (int sft = 1; sft < 4; ++sft) {
-                            // sender k sends M[k][(k - sft) & 3]; receiver r reads lane (r + sft) & 3
-                            const int ei = (r4 - sft) & 3;
-                            const float snd = ei == 0 ? v[4 * q] : ei == 1 ? v[4 * q + 1] : ei == 2 ? v[4 * q + 2] : v[4 * q + 3];
-                            const float got = __shfl_sync(0xffffffffu, snd, qbase + ((r4 + sft) & 3));
-                            const int k = (r4 + sft) & 3;   // the received value is M[k][r4]
-                            t0v = k == 0 ? got : t0v;
-                            t1v = k == 1 ? got : t1v;
-                            t2v = k == 2 ? got : t2v;
-                            t3v = k == 3 ? got : t3v;
-                        }
-                        // own element M[r4][r4]
-                        t0v = r4 == 0 ? own : t0v;
-                        t1v = r4 == 1 ? own : t1v;
-                        t2v = r4 == 2 ? own : t2v;
-                        t3v = r4 == 3 ? own : t3v;
-                        const int ci = cc * 32 + 4 * q + r4;
-                        if (tcol + ci < G.n_cols)
-                            *reinterpret_cast<float4 *>(sv + (tb2 | S.pd[ci])) = make_float4(t0v, t1v, t2v, t3v);
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&S.acc_empty[a]));
+                continue;
+            }
+#pragma unroll 1
+            for (int cc = 0; cc < 4; ++cc) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * kNT + half * 64 + cc * 16), v);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) stg[lane * kStgPitch + c] = v[c];
+                __syncwarp();
+                const int c0 = half * 64 + cc * 16;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int jj = EPI == EPI_COLS ? 2 * r + (lane >> 4) : (lane & 15);
+                    const int col = EPI == EPI_COLS ? (lane & 15) : 2 * r + (lane >> 4);
+                    const float re = stg[(2 * jj) * kStgPitch + col];
+                    const float im = stg[(2 * jj + 1) * kStgPitch + col];
+                    const int ci = c0 + col;
+                    if (tcol + ci < G.n_cols) sv[(tb | S.pd[ci]) + offr[r]] = make_float2(re, im);
+                }
+                __syncwarp();
             }
             tc_fence_before();
             mbar_arrive(smem_u32(&S.acc_empty[a]));
@@ -555,10 +578,10 @@ std::vector<unsigned char> build_a_image(const double *g, sv_precision_t prec) {
     return img;
 }
 
-template <int P, bool VEC4>
+template <int P, bool PROD_COLS, int EPI>
 cudaError_t run_tc(const LaunchCtx &L, float2 *sv, const TcGeom &G, const uint4 *d_a, int *d_err) {
-    auto kern = k_tc6<P, VEC4>;
-    const int smem = kAImg + 2 * kBStage + 1024;
+    auto kern = k_tc6<P, PROD_COLS, EPI>;
+    const int smem = kAImg + 2 * kBStage + kEpiStage + 1024;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     uint64_t grid = (uint64_t)L.num_sms;
@@ -593,11 +616,28 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     const std::vector<unsigned char> img = build_a_image(mat, prec);
     cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
     if (e != cudaSuccess) return e;
-    const bool vec4 = tpos[0] >= 1;
     float2 *s = reinterpret_cast<float2 *>(sv);
     const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
-    if (prec == SV_PREC_TF32) return vec4 ? run_tc<TF32, true>(L, s, G, a, d_err) : run_tc<TF32, false>(L, s, G, a, d_err);
-    return vec4 ? run_tc<BF16, true>(L, s, G, a, d_err) : run_tc<BF16, false>(L, s, G, a, d_err);
+    // Loads: lowest target >= 4 means 16 consecutive columns are contiguous, so lanes
+    // take columns; below that, loads follow address order. Stores: with qubit 0 a
+    // target, runs of members; otherwise direct column pairs when the 16 rows a warp
+    // writes span less than 8 MiB (fourth target below 20), else staged column runs.
+    const int t0 = tpos[0];
+    const bool cols = t0 >= 4;
+    const int epi = t0 == 0 ? EPI_MEMBERS : (tpos[3] < 20 ? EPI_DIRECT : EPI_COLS);
+#define SV_TC_RUN(PR)                                                                           \
+    do {                                                                                        \
+        if (cols) {                                                                             \
+            if (epi == EPI_DIRECT) return run_tc<PR, true, EPI_DIRECT>(L, s, G, a, d_err);      \
+            return run_tc<PR, true, EPI_COLS>(L, s, G, a, d_err);                              \
+        }                                                                                       \
+        if (epi == EPI_DIRECT) return run_tc<PR, false, EPI_DIRECT>(L, s, G, a, d_err);         \
+        if (epi == EPI_COLS) return run_tc<PR, false, EPI_COLS>(L, s, G, a, d_err);             \
+        return run_tc<PR, false, EPI_MEMBERS>(L, s, G, a, d_err);                              \
+    } while (0)
+    if (prec == SV_PREC_TF32) SV_TC_RUN(TF32);
+    SV_TC_RUN(BF16);
+#undef SV_TC_RUN
 }
 
 cudaError_t launch_wait_probe(const LaunchCtx &L, int *d_err, long long cycles) {

@@ -213,64 +213,56 @@ sv_status_t sync_results(sv_ctx *h, int count) {
     return cuda_status(cudaStreamSynchronize(h->stream));
 }
 
-// Tensor-core blocks whose targets all sit at or above this qubit read 64 rows
-// that are at least 1 MiB apart (complex64); measured on GB300 they run at about
-// half the speed of blocks with a lower target.
-constexpr int kFarQubit = 17;
+// Tensor-core blocks whose lowest target is below this qubit cannot read 16
+// consecutive columns as one run (and with qubit 0 among the targets store by
+// members); measured on GB300 they take 1.2-1.4x the time of the others.
+constexpr int kLowQubit = 4;
 
 // Qubit relabelling for a fused run (Sec. II-C, qubit reordering, applied on one
-// GPU): disjoint swaps (low, high) chosen greedily so that as many wide blocks
-// as possible get a target below kFarQubit. Returns the pairs (empty when the
-// saving does not pay for the two extra passes) and the map logical -> physical.
+// GPU): qubits 0..kLowQubit-1 are swapped with the kLowQubit qubits that the
+// fewest wide blocks use (moving only some of them rarely helps, a block then
+// keeps another low target). Returns the pairs -- empty when the blocks it
+// speeds up do not pay for the two extra passes -- and the map logical ->
+// physical.
 void choose_layout(const std::vector<svf::Item> &items, int n, std::vector<int> &pairs, std::vector<int> &map) {
     map.resize(n);
     for (int q = 0; q < n; ++q) map[q] = q;
     pairs.clear();
-    if (n <= kFarQubit) return;
+    if (n < 2 * kLowQubit + 6) return;
     std::vector<const std::vector<int> *> wide;
+    std::vector<int> uses(n, 0);
     for (const svf::Item &it : items)
-        if (!it.passthrough && it.qubits.size() >= 5) wide.push_back(&it.qubits);
-    auto far_count = [&](const std::vector<int> &m) {
+        if (!it.passthrough && !it.diagonal && it.qubits.size() >= 5) {
+            wide.push_back(&it.qubits);
+            for (int q : it.qubits) ++uses[q];
+        }
+    auto slow_count = [&](const std::vector<int> &m) {
         int c = 0;
         for (const std::vector<int> *qs : wide) {
             int lo = 1 << 30;
             for (int q : *qs) lo = std::min(lo, m[q]);
-            c += lo >= kFarQubit;
+            c += lo < kLowQubit;
         }
         return c;
     };
-    const int before = far_count(map);
-    int cur = before;
-    std::vector<char> used(n, 0);
-    for (;;) {
-        int best = cur, bl = -1, bh = -1;
-        for (int l = 0; l < kFarQubit; ++l) {
-            if (used[l]) continue;
-            for (int hq = kFarQubit; hq < n; ++hq) {
-                if (used[hq]) continue;
-                std::vector<int> m = map;
-                for (int q = 0; q < n; ++q) {
-                    if (map[q] == l) m[q] = hq;
-                    else if (map[q] == hq) m[q] = l;
-                }
-                const int c = far_count(m);
-                if (c < best) { best = c; bl = l; bh = hq; }
-            }
-        }
-        if (bl < 0 || (int)pairs.size() / 2 >= 18) break;
-        for (int q = 0; q < n; ++q) {
-            if (map[q] == bl) map[q] = bh;
-            else if (map[q] == bh) map[q] = bl;
-        }
-        used[bl] = used[bh] = 1;
-        pairs.push_back(bl);
-        pairs.push_back(bh);
-        cur = best;
+    std::vector<int> cand;
+    for (int q = kLowQubit; q < n; ++q) cand.push_back(q);
+    std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
+        return uses[a] != uses[b] ? uses[a] < uses[b] : a > b;
+    });
+    std::vector<int> m = map;
+    std::vector<int> trial;
+    for (int l = 0; l < kLowQubit; ++l) {
+        const int h = cand[l];
+        std::swap(m[l], m[h]);
+        trial.push_back(l);
+        trial.push_back(h);
     }
-    // a far block costs about 1.5 near blocks more; the two swap passes about 2
-    if (3 * (before - cur) < 4) {
-        pairs.clear();
-        for (int q = 0; q < n; ++q) map[q] = q;
+    const int before = slow_count(map), after = slow_count(m);
+    // a slow block costs about 0.3 fast blocks more; the two swap passes about 2
+    if (3 * (before - after) >= 20) {
+        map = m;
+        pairs = trial;
     }
 }
 
