@@ -60,16 +60,30 @@ constexpr int kErrTimeout = 0x7c01;
 
 enum Prec { TF32 = 1, BF16 = 2 };
 
-struct TcSmem {
+// Control block in dynamic shared memory after the operand area, and (for the
+// address-order producer only) tile tables in static shared memory, so that
+// each instantiation asks for only what it uses. At 196 KB or less per CTA the
+// SM keeps 60 KB of L1, which the column producer's 64 KB of loads in flight
+// need; the staged epilogues (17 KB more) move the CTA to the 228 KB carve-out.
+struct TcCtl {
     unsigned long long full[2], empty[2], acc_full[2], acc_empty[2], done;
-    uint64_t pd[kNT];   // column offset i in a tile -> amplitude offset (bits deposited around the targets)
+    uint16_t pd[kNT];   // column offset i in a tile -> amplitude offset (the 7 lowest non-target
+                        // positions are below 13, so the offset fits 16 bits)
+    unsigned tmem_base;
+    int abort;
+};
+struct TcTab {
     // A tile's 8192 amplitudes in address order: index a (13 bits) deposited into
     // the 13 tile bit positions (the 6 targets and the 7 lowest other bits).
     uint64_t adr_lo[128], adr_hi[64];   // a's bits 0..6 / 7..12 -> amplitude offset
     uint16_t ij_lo[128], ij_hi[64];     // the same bits -> column i | member j << 7
-    unsigned tmem_base;
-    int abort;
 };
+constexpr int kErrSmemAlign = 0x7c02;
+
+// dynamic shared memory of one instantiation: operands, staging, control
+__host__ __device__ constexpr int tc_stage_off() { return kAImg + 2 * kBStage; }
+__host__ __device__ constexpr int tc_ctl_off(int epi_direct) { return tc_stage_off() + (epi_direct ? 0 : kEpiStage); }
+__host__ __device__ constexpr int tc_smem_bytes(int epi_direct) { return tc_ctl_off(epi_direct) + (int)sizeof(TcCtl); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -229,14 +243,19 @@ enum { EPI_DIRECT = 0, EPI_COLS = 1, EPI_MEMBERS = 2 };
 template <int P, bool PROD_COLS, int EPI>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *__restrict__ d_err) {
-    extern __shared__ unsigned char smem_dyn[];
-    __shared__ TcSmem S;
-    // 1024-byte aligned operand area: A image, then two B stages
-    const uint32_t raw = smem_u32(smem_dyn);
-    const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
-    unsigned char *base = smem_dyn + pad;
-    unsigned char *sA = base;
-    unsigned char *sB0 = base + kAImg;     // stage s at sB0 + s * kBStage
+    // The operand area starts the dynamic shared memory and must be 1024-byte
+    // aligned (128-byte swizzle atoms). Checked, uniformly for all threads, before
+    // any barrier or TMEM allocation: a misplaced window records an error and
+    // returns.
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    if (smem_u32(smem_dyn) & 1023u) {
+        if (threadIdx.x == 0) atomicExch(d_err, kErrSmemAlign);
+        return;
+    }
+    TcCtl &S = *reinterpret_cast<TcCtl *>(smem_dyn + tc_ctl_off(EPI == EPI_DIRECT));
+    __shared__ TcTab T;
+    unsigned char *sA = smem_dyn;
+    unsigned char *sB0 = smem_dyn + kAImg;     // stage s at sB0 + s * kBStage
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abort_flag = &S.abort;
 
@@ -252,8 +271,8 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // A tile starts at a multiple of kNT columns, so col_base(t*kNT + i) = col_base(t*kNT) | pd[i]
-    if (threadIdx.x < kNT) S.pd[threadIdx.x] = col_base((uint64_t)threadIdx.x, G);
-    if (threadIdx.x >= kNT && threadIdx.x < kNT + 192) {
+    if (threadIdx.x < kNT) S.pd[threadIdx.x] = (uint16_t)col_base((uint64_t)threadIdx.x, G);
+    if (!PROD_COLS && threadIdx.x >= kNT && threadIdx.x < kNT + 192) {
         // tile bit b (0..12) in ascending position: either target tj (member bit tj)
         // or the k-th lowest non-target (column bit k); positions >= n only occur
         // for states under 13 qubits and land in columns >= n_cols (never loaded)
@@ -274,8 +293,8 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
             if (is_t) ++tj; else ++k;
             ++b;
         }
-        if (hi) { S.adr_hi[v] = adr; S.ij_hi[v] = (uint16_t)ij; }
-        else { S.adr_lo[v] = adr; S.ij_lo[v] = (uint16_t)ij; }
+        if (hi) { T.adr_hi[v] = adr; T.ij_hi[v] = (uint16_t)ij; }
+        else { T.adr_lo[v] = adr; T.ij_lo[v] = (uint16_t)ij; }
     }
     // A image -> shared memory (plain copy; the host built the swizzled layout)
     for (int i = threadIdx.x; i < kAImg / 16; i += kThreadsTC) reinterpret_cast<uint4 *>(sA)[i] = a_img[i];
@@ -353,9 +372,9 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
     #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     const int a = 2 * ((int)threadIdx.x + kProd * r);
-                    const int ij = S.ij_lo[a & 127] | S.ij_hi[a >> 7];
+                    const int ij = T.ij_lo[a & 127] | T.ij_hi[a >> 7];
                     v[r] = (tcol + (ij & 127) < G.n_cols)
-                               ? *reinterpret_cast<const float4 *>(sv + (tb | S.adr_lo[a & 127] | S.adr_hi[a >> 7]))
+                               ? *reinterpret_cast<const float4 *>(sv + (tb | T.adr_lo[a & 127] | T.adr_hi[a >> 7]))
                                : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 unsigned char *sb = sB0 + s * kBStage;
@@ -364,7 +383,7 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
     #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int a = 2 * ((int)threadIdx.x + kProd * r) + h;
-                        const int ij = S.ij_lo[a & 127] | S.ij_hi[a >> 7];
+                        const int ij = T.ij_lo[a & 127] | T.ij_hi[a >> 7];
                         const int col = ij & 127, j = ij >> 7;
                         const float re = h ? v[r].z : v[r].x, im = h ? v[r].w : v[r].y;
                         if constexpr (P == TF32) {
@@ -436,7 +455,7 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
         const int ew = warp - kProdWarps;
         const int sub = warp & 3;                   // TMEM lanes 32*sub .. 32*sub+31: members 16*sub .. +15
         const int half = ew >> 2;                   // columns 64*half .. 64*half+63 of the tile
-        float *stg = reinterpret_cast<float *>(sB0 + 2 * kBStage) + ew * 32 * kStgPitch;
+        float *stg = reinterpret_cast<float *>(smem_dyn + tc_stage_off()) + ew * 32 * kStgPitch;
         uint64_t offr[8];                           // member offsets this lane stores
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
@@ -581,7 +600,7 @@ std::vector<unsigned char> build_a_image(const double *g, sv_precision_t prec) {
 template <int P, bool PROD_COLS, int EPI>
 cudaError_t run_tc(const LaunchCtx &L, float2 *sv, const TcGeom &G, const uint4 *d_a, int *d_err) {
     auto kern = k_tc6<P, PROD_COLS, EPI>;
-    const int smem = kAImg + 2 * kBStage + kEpiStage + 1024;
+    const int smem = tc_smem_bytes(EPI == EPI_DIRECT);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     uint64_t grid = (uint64_t)L.num_sms;
