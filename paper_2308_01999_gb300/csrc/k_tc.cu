@@ -526,6 +526,272 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// ---------------- raw-operand variant (TF32, qubit 0 not a target) ----------------
+// The same product written with the member index as the contraction:
+//   D(128 x 256) = A(128 x 64) * B(64 x 256),  B[l][2i + f] = component f of
+//   amplitude (member l, column i),  A row m = 32q + r: member j = 16q + r % 16,
+//   Re G[j][.] for r < 16 and Im G[j][.] for r >= 16,
+// so D holds (Re G) x and (Im G) x for the re and im parts of x, and
+//   out_j = (Re G x_re - Im G x_im, Re G x_im + Im G x_re)
+// combines two rows that sit 16 TMEM lanes apart in the same warp's quarter.
+// B in shared memory is the state itself, MN-major (columns contiguous) in the
+// 128-byte swizzle with 32-byte atomicity, the swizzle tf32 MMA takes for
+// MN-major operands (with the plain 128-byte swizzle it produced no result on
+// GB300): each 16-byte chunk is two adjacent amplitudes of one member, copied
+// from HBM by cp.async.cg (no registers, no L1 allocation) and rounded to TF32
+// in place by the thread that copied it (the tensor core drops the low 13 bits,
+// which measured as a norm drift of -3.5e-4 per gate unrounded). Three such
+// stages rotate: load + round, MMA, then the epilogue writes the tile's result
+// into the same stage and stores it back in runs of columns. Needs qubit 0 free (a chunk is two adjacent amplitudes); the
+// launcher uses it from lowest target 3 up.
+constexpr int kNT3 = 128;                     // columns per tile (MMA N = 2 * kNT3 reals)
+constexpr int kStages3 = 3;
+constexpr int kA3 = 128 * 64 * 4;             // A image: 128 rows x 64 tf32, K-major
+constexpr int kB3 = 64 * 2 * kNT3 * 4;        // one stage: 64 members x 256 floats
+constexpr int kProdWarps3 = 4;
+constexpr int kEpiWarps3 = 8;
+constexpr int kMmaWarp3 = kProdWarps3 + kEpiWarps3;
+constexpr int kThreads3 = (kMmaWarp3 + 1) * 32;
+constexpr int kTmemCols3 = 2 * 2 * kNT3;      // two accumulators of 256 columns
+constexpr int kRawMinLowTarget = 3;          // lowest target the launcher sends here
+
+struct TcCtl3 {
+    unsigned long long full[kStages3], empty[kStages3], acc_full[2], acc_empty[2], done;
+    unsigned tmem_base;
+    int abort;
+};
+constexpr int kGuard3 = 2048;              // unused bytes after the last stage
+constexpr int kSmem3 = kA3 + kStages3 * kB3 + kGuard3 + (int)sizeof(TcCtl3);
+
+// byte offset of the 16-byte chunk holding floats 4c .. 4c+3 of member row l
+// (c = amplitude pair, 0..63) in a stage. MN-major TF32 operands use the 128-byte
+// swizzle with 32-byte atomicity: rows of 128 bytes (32 floats of one member),
+// whose four 32-byte units are permuted by the row index mod 4; atoms along the
+// columns 1024 bytes apart, member groups of 8 rows 8192 bytes apart.
+__device__ __forceinline__ uint32_t mn_chunk(int l, int c) {
+    return (uint32_t)((l >> 3) * 8192 + (c >> 3) * 1024 + (l & 7) * 128 + ((((c & 7) >> 1) ^ (l & 3)) << 5) +
+                      ((c & 1) << 4));
+}
+
+// MN-major operand descriptor (128-byte swizzle, 32-byte atomicity): column atoms
+// 1024 bytes apart (leading offset); the rows of an 8-row member group are
+// contiguous, so the stride offset (512 bytes, four rows) reads them in place
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(1024u >> 4) << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= 1ull << 46;
+    d |= 1ull << 61;
+    return d;
+}
+
+// D = F32, A = B = TF32, A K-major, B MN-major (bit 16), N = 256, M = 128
+__host__ __device__ constexpr uint32_t idesc3() {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (1u << 16) | ((uint32_t)((2 * kNT3) >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads3, 1)
+k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *__restrict__ d_err) {
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    if (smem_u32(smem_dyn) & 1023u) {
+        if (threadIdx.x == 0) atomicExch(d_err, kErrSmemAlign);
+        return;
+    }
+    TcCtl3 &S = *reinterpret_cast<TcCtl3 *>(smem_dyn + kA3 + kStages3 * kB3 + kGuard3);
+    unsigned char *sA = smem_dyn;
+    const uint32_t sB0 = smem_u32(smem_dyn + kA3);     // stage s at sB0 + s * kB3
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *abort_flag = &S.abort;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages3; ++i) {
+            mbar_init(smem_u32(&S.full[i]), kProdWarps3 * 32);
+            mbar_init(smem_u32(&S.empty[i]), kEpiWarps3 * 32);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&S.acc_full[i]), 1);
+            mbar_init(smem_u32(&S.acc_empty[i]), kEpiWarps3 * 32);
+        }
+        mbar_init(smem_u32(&S.done), 1);
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < kA3 / 16; i += kThreads3) reinterpret_cast<uint4 *>(sA)[i] = a_img[i];
+    fence_proxy_async();
+    if (warp == kMmaWarp3) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                     "r"(kTmemCols3)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+    const uint64_t ntl = G.n_tiles;
+
+    if (warp < kProdWarps3) {
+        // ---------------- producers: copy, then round the previous tile ----------------
+        // lane takes amplitude pairs c = lane and lane + 32 (columns 2c, 2c + 1) of
+        // members 16 * warp .. 16 * warp + 15
+        uint64_t pc[2];
+        bool okc[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            pc[h] = col_base((uint64_t)(2 * c), G);
+            okc[h] = (uint64_t)(2 * c) < G.n_cols;
+        }
+        auto round_tile = [&](int s) {
+            const uint32_t sb = sB0 + (uint32_t)(s * kB3);
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r) {
+                const uint32_t a = sb + mn_chunk(16 * warp + (r >> 1), lane + 32 * (r & 1));
+                uint32_t x, y, z, w;
+                asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a));
+                x = to_tf32(__uint_as_float(x));
+                y = to_tf32(__uint_as_float(y));
+                z = to_tf32(__uint_as_float(z));
+                w = to_tf32(__uint_as_float(w));
+                asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w)
+                             : "memory");
+            }
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&S.full[s]));
+        };
+        int i = 0;
+        bool ok = true;
+        for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+            const int s = i % kStages3, u = i / kStages3;
+            if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) {
+                ok = false;
+                break;
+            }
+            const uint64_t tb = col_base(t * kNT3, G);
+            const uint32_t sb = sB0 + (uint32_t)(s * kB3);
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r) {
+                const int l = 16 * warp + (r >> 1), h = r & 1;
+                const float2 *src = okc[h] ? sv + (tb | pc[h] | G.off[l]) : sv;
+                cp_async16(sb + mn_chunk(l, lane + 32 * h), src, okc[h] ? 16u : 0u);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (i >= 1) {
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+                round_tile((i - 1) % kStages3);
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (ok && i >= 1) round_tile((i - 1) % kStages3);
+    } else if (warp == kMmaWarp3) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t a_addr = smem_u32(sA);
+            int i = 0;
+            for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+                const int s = i % kStages3, a = i & 1;
+                if (!mbar_wait(smem_u32(&S.full[s]), (i / kStages3) & 1, abort_flag, d_err)) break;
+                if (i >= 2 && !mbar_wait(smem_u32(&S.acc_empty[a]), ((i >> 1) - 1) & 1, abort_flag, d_err)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(a * 2 * kNT3);
+                const uint32_t b_addr = sB0 + (uint32_t)(s * kB3);
+                // K = 64 members in 8 steps of 8: A K-block ks / 4 (16 KB apart), 32 bytes
+                // per step within its rows; B member group ks (8192 bytes apart)
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks) {
+                    const uint64_t ad = sdesc(a_addr + (uint32_t)((ks >> 2) * 16384 + (ks & 3) * 32));
+                    const uint64_t bd = sdesc_mn(b_addr + (uint32_t)(ks * 8192));
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                        "l"(ad), "l"(bd), "r"(idesc3()), "r"(ks)
+                        : "memory");
+                }
+                mma_commit(smem_u32(&S.acc_full[a]));
+            }
+            mma_commit(smem_u32(&S.done));
+            const long long t0 = clock64();
+            while (!mbar_try(smem_u32(&S.done), 0) && clock64() - t0 < kWaitCycles) {
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue ----------------
+        // warp: TMEM lane quarter q (members 16q .. 16q + 15, Re rows then Im rows),
+        // column half hh (amplitudes 64 hh .. 64 hh + 63 of the tile)
+        const int ew = warp - kProdWarps3;
+        const int q = warp & 3, hh = ew >> 2;
+        const int e = lane >> 4, j = 16 * q + (lane & 15);
+        const int cst = 32 * hh + lane;                        // amplitude pair this lane stores
+        const uint64_t pst = col_base((uint64_t)(2 * cst), G);
+        const bool okst = (uint64_t)(2 * cst) < G.n_cols;
+        int i = 0;
+        for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+            const int s = i % kStages3, a = i & 1;
+            if (!mbar_wait(smem_u32(&S.acc_full[a]), (i >> 1) & 1, abort_flag, d_err)) break;
+            tc_fence_after();
+            const uint32_t sb = sB0 + (uint32_t)(s * kB3);
+            const uint64_t tb = col_base(t * kNT3, G);
+#pragma unroll 1
+            for (int cc = 0; cc < 4; ++cc) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 2 * kNT3 + hh * kNT3 + cc * 32), v);
+                // v[2u + f] = row product for amplitude 64 hh + 16 cc + u, component f. Of each
+                // four amplitudes 4P .. 4P+3 the Re lane finishes the first two, the Im lane
+                // the last two; each sends the partner the four products it needs.
+#pragma unroll
+                for (int P = 0; P < 4; ++P) {
+                    float r[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        r[k] = __shfl_xor_sync(0xffffffffu, e ? v[8 * P + k] : v[8 * P + 4 + k], 16);
+                    float4 o;
+                    if (e == 0) {
+                        o = make_float4(v[8 * P] - r[1], v[8 * P + 1] + r[0], v[8 * P + 2] - r[3], v[8 * P + 3] + r[2]);
+                    } else {
+                        o = make_float4(r[0] - v[8 * P + 5], r[1] + v[8 * P + 4], r[2] - v[8 * P + 7],
+                                        r[3] + v[8 * P + 6]);
+                    }
+                    // amplitude pair c of the tile, staged as one 16-byte chunk (conflict free:
+                    // the 16 rows of an instruction fall in four 32-byte bank groups)
+                    const int c = 32 * hh + 8 * cc + 2 * P + e;
+                    asm volatile("st.shared.v4.f32 [%0], {%1,%2,%3,%4};" ::"r"(sb + mn_chunk(j, c)), "f"(o.x),
+                                 "f"(o.y), "f"(o.z), "f"(o.w)
+                                 : "memory");
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&S.acc_empty[a]));
+            __syncwarp();
+            // store: one member row per instruction, lanes on consecutive amplitude pairs
+            // (runs of 512 bytes when the lowest target is 6 or more). A store that
+            // scatters over 16 rows runs far below HBM bandwidth once the rows are MiB
+            // apart; these never do.
+#pragma unroll 4
+            for (int r = 0; r < 16; ++r) {
+                const int l = 16 * q + r;
+                float4 o;
+                asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                             : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
+                             : "r"(sb + mn_chunk(l, cst)));
+                if (okst) *reinterpret_cast<float4 *>(sv + (tb | pst | G.off[l])) = o;
+            }
+            mbar_arrive(smem_u32(&S.empty[s]));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kMmaWarp3)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols3) : "memory");
+}
+
 // Diagnostic of the bounded wait: one thread waits on an mbarrier whose phase
 // never completes (nothing arrives), with a budget of `cycles` clock ticks, so
 // the wait must give up and record kErrTimeout in the status word.
@@ -597,6 +863,30 @@ std::vector<unsigned char> build_a_image(const double *g, sv_precision_t prec) {
     return img;
 }
 
+// A image of the raw-operand variant: row m = 32q + r holds Re G[16q + r % 16][.]
+// (r < 16) or Im G[16q + r % 16][.] (r >= 16); K = 64 members, two 128-byte K-blocks
+std::vector<unsigned char> build_a_image3(const double *g) {
+    std::vector<unsigned char> img(kA3, 0);
+    for (int m = 0; m < 128; ++m) {
+        const int j = 16 * (m >> 5) + (m & 15), part = (m >> 4) & 1;
+        for (int k = 0; k < 64; ++k) {
+            const uint32_t w = host_tf32((float)g[2 * (j * 64 + k) + part]);
+            std::memcpy(&img[host_sw128(k >> 5, m, (k & 31) >> 2) + (k & 3) * 4], &w, 4);
+        }
+    }
+    return img;
+}
+
+cudaError_t run_tc_raw(const LaunchCtx &L, float2 *sv, const TcGeom &G, const uint4 *d_a, int *d_err) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc6_raw, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+    if (e != cudaSuccess) return e;
+    uint64_t grid = (uint64_t)L.num_sms;
+    if (grid > G.n_tiles) grid = G.n_tiles;
+    k_tc6_raw<<<(unsigned)grid, kThreads3, kSmem3, L.stream>>>(sv, G, d_a, d_err);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
 template <int P, bool PROD_COLS, int EPI>
 cudaError_t run_tc(const LaunchCtx &L, float2 *sv, const TcGeom &G, const uint4 *d_a, int *d_err) {
     auto kern = k_tc6<P, PROD_COLS, EPI>;
@@ -632,11 +922,23 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     }
     G.n_cols = 1ull << (n - 6);
     G.n_tiles = (G.n_cols + kNT - 1) / kNT;
+    float2 *s = reinterpret_cast<float2 *>(sv);
+    const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
+    // TF32 with the lowest target at 3 or above (amplitude pairs of one member are
+    // adjacent, runs of at least 64 bytes): the raw-operand kernel, measured on
+    // GB300 at one time per block whatever the other targets (11.7 ms for a
+    // 32-qubit state when the lowest target is 4 or more, 13.2 ms at 3). With the
+    // lowest target at 1 or 2 its 16-32-byte runs make it slower than the
+    // register-staged kernel below.
+    if (prec == SV_PREC_TF32 && tpos[0] >= kRawMinLowTarget && n >= 8) {
+        const std::vector<unsigned char> img = build_a_image3(mat);
+        cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
+        if (e != cudaSuccess) return e;
+        return run_tc_raw(L, s, G, a, d_err);
+    }
     const std::vector<unsigned char> img = build_a_image(mat, prec);
     cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
     if (e != cudaSuccess) return e;
-    float2 *s = reinterpret_cast<float2 *>(sv);
-    const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
     // Loads: lowest target >= 4 means 16 consecutive columns are contiguous, so lanes
     // take columns; below that, loads follow address order. Stores: with qubit 0 a
     // target, runs of members; otherwise direct column pairs when the 16 rows a warp

@@ -213,22 +213,27 @@ sv_status_t sync_results(sv_ctx *h, int count) {
     return cuda_status(cudaStreamSynchronize(h->stream));
 }
 
-// Tensor-core blocks whose lowest target is below this qubit cannot read 16
-// consecutive columns as one run (and with qubit 0 among the targets store by
-// members); measured on GB300 they take 1.2-1.4x the time of the others.
-constexpr int kLowQubit = 4;
+// Tensor-core blocks whose lowest target is below `low` take a slower kernel
+// variant: for TF32 below qubit 3 (the raw-operand kernel needs runs of at least
+// 64 bytes; measured on GB300 at 32 qubits: 11.7 ms per block from lowest target
+// 4 up, 16-16.4 ms for lowest target 0-2), for split BF16 below qubit 4 (12.3-12.8
+// ms against 15-19 ms).
+int slow_below(sv_precision_t prec) { return prec == SV_PREC_TF32 ? 3 : 4; }
 
 // Qubit relabelling for a fused run (Sec. II-C, qubit reordering, applied on one
-// GPU): qubits 0..kLowQubit-1 are swapped with the kLowQubit qubits that the
-// fewest wide blocks use (moving only some of them rarely helps, a block then
-// keeps another low target). Returns the pairs -- empty when the blocks it
-// speeds up do not pay for the two extra passes -- and the map logical ->
-// physical.
-void choose_layout(const std::vector<svf::Item> &items, int n, std::vector<int> &pairs, std::vector<int> &map) {
+// GPU): qubits 0..low-1 are swapped with the `low` qubits that the fewest wide
+// blocks use (moving only some of them rarely helps, a block then keeps another
+// low target). Returns the pairs -- empty when the blocks it speeds up do not pay
+// for the two extra passes -- and the map logical -> physical. Cost model from
+// the measurements above: a slow block costs about 0.3 of a fast block more, the
+// two swap passes (one permutation pass each way over the whole state) about 1.8
+// fast blocks, so at least 6 fewer slow blocks are needed.
+void choose_layout(const std::vector<svf::Item> &items, int n, int low, std::vector<int> &pairs,
+                   std::vector<int> &map) {
     map.resize(n);
     for (int q = 0; q < n; ++q) map[q] = q;
     pairs.clear();
-    if (n < 2 * kLowQubit + 6) return;
+    if (n < 2 * low + 6) return;
     std::vector<const std::vector<int> *> wide;
     std::vector<int> uses(n, 0);
     for (const svf::Item &it : items)
@@ -241,26 +246,25 @@ void choose_layout(const std::vector<svf::Item> &items, int n, std::vector<int> 
         for (const std::vector<int> *qs : wide) {
             int lo = 1 << 30;
             for (int q : *qs) lo = std::min(lo, m[q]);
-            c += lo < kLowQubit;
+            c += lo < low;
         }
         return c;
     };
     std::vector<int> cand;
-    for (int q = kLowQubit; q < n; ++q) cand.push_back(q);
+    for (int q = low; q < n; ++q) cand.push_back(q);
     std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
         return uses[a] != uses[b] ? uses[a] < uses[b] : a > b;
     });
     std::vector<int> m = map;
     std::vector<int> trial;
-    for (int l = 0; l < kLowQubit; ++l) {
+    for (int l = 0; l < low; ++l) {
         const int h = cand[l];
         std::swap(m[l], m[h]);
         trial.push_back(l);
         trial.push_back(h);
     }
     const int before = slow_count(map), after = slow_count(m);
-    // a slow block costs about 0.3 fast blocks more; the two swap passes about 2
-    if (3 * (before - after) >= 20) {
+    if (before - after >= 6) {
         map = m;
         pairs = trial;
     }
@@ -507,7 +511,7 @@ sv_status_t sv_apply_fused_ex(sv_handle_t h, const sv_gate_t *gates, int n_gates
     if (s != SV_OK) return s;
     DeviceGuard dg(h->device);
     std::vector<int> pairs, map;
-    if (prec != SV_PREC_NATIVE) choose_layout(items, h->n, pairs, map);
+    if (prec != SV_PREC_NATIVE) choose_layout(items, h->n, slow_below(prec), pairs, map);
     else {
         map.resize(h->n);
         for (int q = 0; q < h->n; ++q) map[q] = q;
