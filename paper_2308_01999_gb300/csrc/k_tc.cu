@@ -537,26 +537,30 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
 // B in shared memory is the state itself, MN-major (columns contiguous) in the
 // 128-byte swizzle with 32-byte atomicity, the swizzle tf32 MMA takes for
 // MN-major operands (with the plain 128-byte swizzle it produced no result on
-// GB300): each 16-byte chunk is two adjacent amplitudes of one member, copied
-// from HBM by cp.async.cg (no registers, no L1 allocation) and rounded to TF32
-// in place by the thread that copied it (the tensor core drops the low 13 bits,
-// which measured as a norm drift of -3.5e-4 per gate unrounded). Three such
-// stages rotate: load + round, MMA, then the epilogue writes the tile's result
-// into the same stage and stores it back in runs of columns. Needs qubit 0 free (a chunk is two adjacent amplitudes); the
+// GB300): each 16-byte chunk is two adjacent amplitudes of one member. Roles
+// (15 warps): 2 copy warps issue cp.async.cg (no registers, no L1 allocation)
+// and let the copies arrive on the stage's `landed` barrier, so they never wait
+// for data; 4 round warps round the landed stage to TF32 in place (the tensor
+// core drops the low 13 bits, which measured as a norm drift of -3.5e-4 per gate
+// unrounded); one thread issues the MMAs; 8 epilogue warps combine, write the
+// tile's result into the stage it came from and store it back in runs of
+// columns. Three stages rotate. Needs qubit 0 free (a chunk is two adjacent amplitudes); the
 // launcher uses it from lowest target 3 up.
 constexpr int kNT3 = 128;                     // columns per tile (MMA N = 2 * kNT3 reals)
 constexpr int kStages3 = 3;
 constexpr int kA3 = 128 * 64 * 4;             // A image: 128 rows x 64 tf32, K-major
 constexpr int kB3 = 64 * 2 * kNT3 * 4;        // one stage: 64 members x 256 floats
-constexpr int kProdWarps3 = 4;
-constexpr int kEpiWarps3 = 8;
+constexpr int kCopyWarps3 = 2;                // warps 0-1: cp.async issue
+constexpr int kRoundWarps3 = 4;               // warps 2-5: TF32 rounding in place
+constexpr int kProdWarps3 = kCopyWarps3 + kRoundWarps3;
+constexpr int kEpiWarps3 = 8;                 // warps 6-13
 constexpr int kMmaWarp3 = kProdWarps3 + kEpiWarps3;
 constexpr int kThreads3 = (kMmaWarp3 + 1) * 32;
 constexpr int kTmemCols3 = 2 * 2 * kNT3;      // two accumulators of 256 columns
 constexpr int kRawMinLowTarget = 3;          // lowest target the launcher sends here
 
 struct TcCtl3 {
-    unsigned long long full[kStages3], empty[kStages3], acc_full[2], acc_empty[2], done;
+    unsigned long long landed[kStages3], full[kStages3], empty[kStages3], acc_full[2], acc_empty[2], done;
     unsigned tmem_base;
     int abort;
 };
@@ -611,7 +615,8 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages3; ++i) {
-            mbar_init(smem_u32(&S.full[i]), kProdWarps3 * 32);
+            mbar_init(smem_u32(&S.landed[i]), kCopyWarps3 * 32);
+            mbar_init(smem_u32(&S.full[i]), kRoundWarps3 * 32);
             mbar_init(smem_u32(&S.empty[i]), kEpiWarps3 * 32);
         }
         for (int i = 0; i < 2; ++i) {
@@ -636,59 +641,54 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
     const uint32_t tmem = S.tmem_base;
     const uint64_t ntl = G.n_tiles;
 
-    if (warp < kProdWarps3) {
-        // ---------------- producers: copy, then round the previous tile ----------------
-        // lane takes amplitude pairs c = lane and lane + 32 (columns 2c, 2c + 1) of
-        // members 16 * warp .. 16 * warp + 15
-        uint64_t pc[2];
-        bool okc[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
-            pc[h] = col_base((uint64_t)(2 * c), G);
-            okc[h] = (uint64_t)(2 * c) < G.n_cols;
+    if (warp < kCopyWarps3) {
+        // ---------------- copy: thread c takes amplitude pair c of all 64 members ----------------
+        // (a warp load is 32 consecutive pairs of one member: 512 contiguous bytes once
+        // the lowest target is 6 or more). The copies signal `landed` themselves
+        // (cp.async.mbarrier.arrive), so these threads never wait for data.
+        const int c = threadIdx.x;
+        const uint64_t pc = col_base((uint64_t)(2 * c), G);
+        const bool okc = (uint64_t)(2 * c) < G.n_cols;
+        int i = 0;
+        for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+            const int s = i % kStages3, u = i / kStages3;
+            if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
+            const uint64_t tb = col_base(t * kNT3, G) | pc;
+            const uint32_t sb = sB0 + (uint32_t)(s * kB3);
+#pragma unroll 16
+            for (int l = 0; l < 64; ++l) {
+                const float2 *src = okc ? sv + (tb | G.off[l]) : sv;
+                cp_async16(sb + mn_chunk(l, c), src, okc ? 16u : 0u);
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.landed[s]))
+                         : "memory");
         }
-        auto round_tile = [&](int s) {
+        // every copy this thread issued has landed before the CTA may exit
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp < kProdWarps3) {
+        // ---------------- round: TF32 round-to-nearest in place ----------------
+        // The tensor core reads a TF32 operand as the float's top 19 bits; adding half of
+        // their last place (0x1000) to the bit pattern first makes that truncation a
+        // rounding to nearest, ties away from zero (what cvt.rna.tf32.f32 computes),
+        // for one integer add per value.
+        const int rt = threadIdx.x - kCopyWarps3 * 32;   // 0..127: pair rt & 63, members 2r + rt / 64
+        int i = 0;
+        for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+            const int s = i % kStages3;
+            if (!mbar_wait(smem_u32(&S.landed[s]), (i / kStages3) & 1, abort_flag, d_err)) break;
             const uint32_t sb = sB0 + (uint32_t)(s * kB3);
 #pragma unroll 8
             for (int r = 0; r < 32; ++r) {
-                const uint32_t a = sb + mn_chunk(16 * warp + (r >> 1), lane + 32 * (r & 1));
+                const uint32_t a = sb + mn_chunk(2 * r + (rt >> 6), rt & 63);
                 uint32_t x, y, z, w;
                 asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a));
-                x = to_tf32(__uint_as_float(x));
-                y = to_tf32(__uint_as_float(y));
-                z = to_tf32(__uint_as_float(z));
-                w = to_tf32(__uint_as_float(w));
-                asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w)
+                asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(x + 0x1000u), "r"(y + 0x1000u),
+                             "r"(z + 0x1000u), "r"(w + 0x1000u)
                              : "memory");
             }
             fence_proxy_async();
             mbar_arrive(smem_u32(&S.full[s]));
-        };
-        int i = 0;
-        bool ok = true;
-        for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
-            const int s = i % kStages3, u = i / kStages3;
-            if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) {
-                ok = false;
-                break;
-            }
-            const uint64_t tb = col_base(t * kNT3, G);
-            const uint32_t sb = sB0 + (uint32_t)(s * kB3);
-#pragma unroll 8
-            for (int r = 0; r < 32; ++r) {
-                const int l = 16 * warp + (r >> 1), h = r & 1;
-                const float2 *src = okc[h] ? sv + (tb | pc[h] | G.off[l]) : sv;
-                cp_async16(sb + mn_chunk(l, lane + 32 * h), src, okc[h] ? 16u : 0u);
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            if (i >= 1) {
-                asm volatile("cp.async.wait_group 1;" ::: "memory");
-                round_tile((i - 1) % kStages3);
-            }
         }
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        if (ok && i >= 1) round_tile((i - 1) % kStages3);
     } else if (warp == kMmaWarp3) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
@@ -926,8 +926,8 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
     // TF32 with the lowest target at 3 or above (amplitude pairs of one member are
     // adjacent, runs of at least 64 bytes): the raw-operand kernel, measured on
-    // GB300 at one time per block whatever the other targets (11.7 ms for a
-    // 32-qubit state when the lowest target is 4 or more, 13.2 ms at 3). With the
+    // GB300 at one time per block whatever the other targets (10.5 ms for a
+    // 32-qubit state when the lowest target is 4 or more, 11.9 ms at 3). With the
     // lowest target at 1 or 2 its 16-32-byte runs make it slower than the
     // register-staged kernel below.
     if (prec == SV_PREC_TF32 && tpos[0] >= kRawMinLowTarget && n >= 8) {

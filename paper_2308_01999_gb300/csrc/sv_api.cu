@@ -215,9 +215,9 @@ sv_status_t sync_results(sv_ctx *h, int count) {
 
 // Tensor-core blocks whose lowest target is below `low` take a slower kernel
 // variant: for TF32 below qubit 3 (the raw-operand kernel needs runs of at least
-// 64 bytes; measured on GB300 at 32 qubits: 11.7 ms per block from lowest target
-// 4 up, 16-16.4 ms for lowest target 0-2), for split BF16 below qubit 4 (12.3-12.8
-// ms against 15-19 ms).
+// 64 bytes; measured on GB300 at 32 qubits: 10.5 ms per block from lowest target
+// 4 up, 11.9 ms at 3, 15.8-16.4 ms for lowest target 0-2), for split BF16 below
+// qubit 4 (12.3-12.8 ms against 15-19 ms).
 int slow_below(sv_precision_t prec) { return prec == SV_PREC_TF32 ? 3 : 4; }
 
 // Qubit relabelling for a fused run (Sec. II-C, qubit reordering, applied on one
@@ -225,9 +225,9 @@ int slow_below(sv_precision_t prec) { return prec == SV_PREC_TF32 ? 3 : 4; }
 // blocks use (moving only some of them rarely helps, a block then keeps another
 // low target). Returns the pairs -- empty when the blocks it speeds up do not pay
 // for the two extra passes -- and the map logical -> physical. Cost model from
-// the measurements above: a slow block costs about 0.3 of a fast block more, the
-// two swap passes (one permutation pass each way over the whole state) about 1.8
-// fast blocks, so at least 6 fewer slow blocks are needed.
+// the measurements above: a slow block costs about 0.3-0.5 of a fast block more,
+// the two swap passes (one permutation pass each way over the whole state) about
+// 2 fast blocks, so at least 6 fewer slow blocks are needed.
 void choose_layout(const std::vector<svf::Item> &items, int n, int low, std::vector<int> &pairs,
                    std::vector<int> &map) {
     map.resize(n);
