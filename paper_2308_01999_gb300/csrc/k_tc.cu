@@ -544,7 +544,8 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
 // core drops the low 13 bits, which measured as a norm drift of -3.5e-4 per gate
 // unrounded); one thread issues the MMAs; 8 epilogue warps combine, write the
 // tile's result into the stage it came from and store it back in runs of
-// columns. Three stages rotate. Needs qubit 0 free (a chunk is two adjacent amplitudes); the
+// columns. Three stages rotate. Needs qubit 0 free (a chunk is two adjacent
+// amplitudes); the launcher uses it from lowest target 2 up. Needs qubit 0 free (a chunk is two adjacent amplitudes); the
 // launcher uses it from lowest target 3 up.
 constexpr int kNT3 = 128;                     // columns per tile (MMA N = 2 * kNT3 reals)
 constexpr int kStages3 = 3;
@@ -557,7 +558,7 @@ constexpr int kEpiWarps3 = 8;                 // warps 6-13
 constexpr int kMmaWarp3 = kProdWarps3 + kEpiWarps3;
 constexpr int kThreads3 = (kMmaWarp3 + 1) * 32;
 constexpr int kTmemCols3 = 2 * 2 * kNT3;      // two accumulators of 256 columns
-constexpr int kRawMinLowTarget = 3;          // lowest target the launcher sends here
+constexpr int kRawMinLowTarget = 2;          // lowest target the launcher sends here
 
 struct TcCtl3 {
     unsigned long long landed[kStages3], full[kStages3], empty[kStages3], acc_full[2], acc_empty[2], done;
@@ -924,12 +925,11 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     G.n_tiles = (G.n_cols + kNT - 1) / kNT;
     float2 *s = reinterpret_cast<float2 *>(sv);
     const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
-    // TF32 with the lowest target at 3 or above (amplitude pairs of one member are
-    // adjacent, runs of at least 64 bytes): the raw-operand kernel, measured on
-    // GB300 at one time per block whatever the other targets (10.5 ms for a
-    // 32-qubit state when the lowest target is 4 or more, 11.9 ms at 3). With the
-    // lowest target at 1 or 2 its 16-32-byte runs make it slower than the
-    // register-staged kernel below.
+    // TF32 with the lowest target at 2 or above (runs of at least 32 bytes): the
+    // raw-operand kernel, measured on GB300 at one time per block whatever the
+    // other targets (10.5 ms for a 32-qubit state when the lowest target is 4 or
+    // more, 11.9 ms at 3, 14.7 ms at 2). With the lowest target at 1 its 16-byte
+    // runs make it slower (18.5 ms) than the register-staged kernel below (16.4).
     if (prec == SV_PREC_TF32 && tpos[0] >= kRawMinLowTarget && n >= 8) {
         const std::vector<unsigned char> img = build_a_image3(mat);
         cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);

@@ -214,11 +214,10 @@ sv_status_t sync_results(sv_ctx *h, int count) {
 }
 
 // Tensor-core blocks whose lowest target is below `low` take a slower kernel
-// variant: for TF32 below qubit 3 (the raw-operand kernel needs runs of at least
-// 64 bytes; measured on GB300 at 32 qubits: 10.5 ms per block from lowest target
-// 4 up, 11.9 ms at 3, 15.8-16.4 ms for lowest target 0-2), for split BF16 below
-// qubit 4 (12.3-12.8 ms against 15-19 ms).
-int slow_below(sv_precision_t prec) { return prec == SV_PREC_TF32 ? 3 : 4; }
+// variant: for TF32 below qubit 2 (measured on GB300 at 32 qubits: 10.5 ms per
+// block from lowest target 4 up, 11.9 ms at 3, 14.7 ms at 2, 16-16.4 ms at 0-1),
+// for split BF16 below qubit 4 (12.3-12.8 ms against 15-19 ms).
+int slow_below(sv_precision_t prec) { return prec == SV_PREC_TF32 ? 2 : 4; }
 
 // Qubit relabelling for a fused run (Sec. II-C, qubit reordering, applied on one
 // GPU): qubits 0..low-1 are swapped with the `low` qubits that the fewest wide

@@ -9,7 +9,7 @@ c = 3 * 2^-18 + 384 * 2^-24 (split BF16); for a unitary gate that sum is at
 most sqrt(128) times the group's norm, so one gate changes the relative L2
 error by at most sqrt(128) * c and G gates by G times that. The tests assert
 these worst-case bounds and print the measured errors. The TF32 kernel for
-lowest targets >= 3 contracts over the 64 members in two FP32 sums of 64 terms
+lowest targets >= 2 contracts over the 64 members in two FP32 sums of 64 terms
 (real and imaginary parts of G) joined by one addition, inside the same bound.
 """
 import math
@@ -48,7 +48,7 @@ def rel_l2(got, ref):
 @pytest.mark.parametrize("n,targets", [(12, (2, 3, 5, 7, 8, 11)), (13, (0, 1, 2, 3, 4, 5)),
                                        (10, (4, 5, 6, 7, 8, 9)), (14, (1, 4, 6, 9, 12, 13)),
                                        (8, (0, 2, 3, 5, 6, 7)), (6, (0, 1, 2, 3, 4, 5)),
-                                       # lowest target >= 3: one ragged tile (8 or 32 columns),
+                                       # lowest target >= 2: one ragged tile (8 or 32 columns),
                                        # several tiles, far and contiguous targets
                                        (9, (3, 4, 5, 6, 7, 8)), (11, (3, 5, 6, 8, 9, 10)),
                                        (16, (5, 9, 10, 12, 14, 15)), (20, (3, 8, 12, 16, 18, 19)),
@@ -111,7 +111,7 @@ def test_native_and_tensor_core_agree_on_structure(env):
 
 @pytest.mark.parametrize("name", ["tf32", "bf16"])
 def test_low_targets_relabelled_by_index_bit_swaps(env, name):
-    """Wide blocks whose lowest target is below qubit 3 (TF32) or 4 (split
+    """Wide blocks whose lowest target is below qubit 2 (TF32) or 4 (split
     BF16) run after a qubit relabelling (two extra index-bit-swap passes) when
     enough of them gain from it; the result is unchanged."""
     torch, sv = env
