@@ -115,6 +115,139 @@ __device__ void op_diag(float2 *tile, const BOp &op, const float2 *msh, int T) {
     }
 }
 
+// ---- windows: a run of small ops on 2^W amplitudes held in registers ----
+// Template arguments fix every register index; the run-time target bits select
+// the instantiation. Control conditions ((r & cm) == cv) are uniform across the
+// CTA, so they only predicate.
+template <int W, int B>
+__device__ __forceinline__ void win_dense1(float2 (&v)[1 << W], const float2 *m, uint32_t cm, uint32_t cv) {
+    if constexpr (B < W) {
+        const float2 m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) {
+            if (r & (1 << B)) continue;
+            if (((uint32_t)r & cm) != cv) continue;
+            const float2 a = v[r], c = v[r | (1 << B)];
+            v[r] = make_float2(__fmaf_rn(m00.x, a.x, __fmaf_rn(-m00.y, a.y, __fmaf_rn(m01.x, c.x, -m01.y * c.y))),
+                               __fmaf_rn(m00.x, a.y, __fmaf_rn(m00.y, a.x, __fmaf_rn(m01.x, c.y, m01.y * c.x))));
+            v[r | (1 << B)] =
+                make_float2(__fmaf_rn(m10.x, a.x, __fmaf_rn(-m10.y, a.y, __fmaf_rn(m11.x, c.x, -m11.y * c.y))),
+                            __fmaf_rn(m10.x, a.y, __fmaf_rn(m10.y, a.x, __fmaf_rn(m11.x, c.y, m11.y * c.x))));
+        }
+    }
+}
+
+template <int W, int B>
+__device__ __forceinline__ void win_swap1(float2 (&v)[1 << W], const float2 *m, uint32_t cm, uint32_t cv) {
+    if constexpr (B < W) {
+        const float2 f0 = m[0], f1 = m[1];
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) {
+            if (r & (1 << B)) continue;
+            if (((uint32_t)r & cm) != cv) continue;
+            const float2 a = v[r], c = v[r | (1 << B)];
+            v[r] = cmulf(f1, c);
+            v[r | (1 << B)] = cmulf(f0, a);
+        }
+    }
+}
+
+template <int W, int B0, int B1>
+__device__ __forceinline__ void win_dense2(float2 (&v)[1 << W], const float2 *m, uint32_t cm, uint32_t cv) {
+    if constexpr (B0 < B1 && B1 < W) {
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) {
+            if (r & ((1 << B0) | (1 << B1))) continue;
+            if (((uint32_t)r & cm) != cv) continue;
+            const int o[4] = {r, r | (1 << B0), r | (1 << B1), r | (1 << B0) | (1 << B1)};
+            float2 a[4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) a[l] = v[o[l]];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const float2 x = m[4 * j + l];
+                    acc.x = __fmaf_rn(x.x, a[l].x, acc.x);
+                    acc.x = __fmaf_rn(-x.y, a[l].y, acc.x);
+                    acc.y = __fmaf_rn(x.x, a[l].y, acc.y);
+                    acc.y = __fmaf_rn(x.y, a[l].x, acc.y);
+                }
+                v[o[j]] = acc;
+            }
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void win_diag(float2 (&v)[1 << W], const float2 *m, int nd, int b0, int b1, uint32_t cm,
+                                         uint32_t cv) {
+#pragma unroll
+    for (int r = 0; r < (1 << W); ++r) {
+        if (((uint32_t)r & cm) != cv) continue;
+        const int j = nd == 0 ? 0 : nd == 1 ? ((r >> b0) & 1) : (((r >> b0) & 1) | (((r >> b1) & 1) << 1));
+        v[r] = cmulf(m[j], v[r]);
+    }
+}
+
+template <int W>
+__device__ void op_window(float2 *tile, const BOp &op, const float2 *blk, int T) {
+    constexpr int D = 1 << W;
+    const int ngroups = 1 << (T - W);
+    const int nsub = op.k;
+    uint32_t off[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        uint32_t o = 0;
+#pragma unroll
+        for (int t = 0; t < W; ++t)
+            if ((j >> t) & 1) o |= 1u << op.p[t];
+        off[j] = o;
+    }
+    for (int g = threadIdx.x; g < ngroups; g += kT) {
+        const uint32_t base = insert_zeros_local((uint32_t)g, op);
+        float2 v[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) v[j] = tile[base | off[j]];
+        for (int s = 0; s < nsub; ++s) {
+            const float2 h0 = blk[2 * s], h1 = blk[2 * s + 1];
+            const uint32_t hx = __float_as_uint(h0.x), hy = __float_as_uint(h0.y);
+            const int kind = hx & 0xff, b0 = (hx >> 8) & 0xff, b1 = (hx >> 16) & 0xff, nd = hx >> 24;
+            const uint32_t cm = hy & 0xff, cv = (hy >> 8) & 0xff;
+            const float2 *m = blk + __float_as_uint(h1.x);
+            if (kind == BSUB_DENSE1) {
+                switch (b0) {
+                case 0: win_dense1<W, 0>(v, m, cm, cv); break;
+                case 1: win_dense1<W, 1>(v, m, cm, cv); break;
+                case 2: win_dense1<W, 2>(v, m, cm, cv); break;
+                default: win_dense1<W, 3>(v, m, cm, cv); break;
+                }
+            } else if (kind == BSUB_DENSE2) {
+                switch (b0 * 4 + b1) {
+                case 1: win_dense2<W, 0, 1>(v, m, cm, cv); break;
+                case 2: win_dense2<W, 0, 2>(v, m, cm, cv); break;
+                case 3: win_dense2<W, 0, 3>(v, m, cm, cv); break;
+                case 6: win_dense2<W, 1, 2>(v, m, cm, cv); break;
+                case 7: win_dense2<W, 1, 3>(v, m, cm, cv); break;
+                default: win_dense2<W, 2, 3>(v, m, cm, cv); break;
+                }
+            } else if (kind == BSUB_SWAP1) {
+                switch (b0) {
+                case 0: win_swap1<W, 0>(v, m, cm, cv); break;
+                case 1: win_swap1<W, 1>(v, m, cm, cv); break;
+                case 2: win_swap1<W, 2>(v, m, cm, cv); break;
+                default: win_swap1<W, 3>(v, m, cm, cv); break;
+                }
+            } else {
+                win_diag<W>(v, m, nd, b0, b1, cm, cv);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) tile[base | off[j]] = v[j];
+    }
+}
+
 __device__ double block_sum(double v, double *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -199,7 +332,14 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
                         __syncthreads();
                         m = msh;
                     }
-                    if (op.kind == BOP_DENSE) {
+                    if (op.kind == BOP_WIN) {
+                        // windows only occur in stages whose matrices are staged
+                        switch (op.np) {
+                        case 2: op_window<2>(tile, op, m, T); break;
+                        case 3: op_window<3>(tile, op, m, T); break;
+                        default: op_window<4>(tile, op, m, T); break;
+                        }
+                    } else if (op.kind == BOP_DENSE) {
                         switch (op.k) {
                         case 1: op_dense<1>(tile, op, m, T); break;
                         case 2: op_dense<2>(tile, op, m, T); break;

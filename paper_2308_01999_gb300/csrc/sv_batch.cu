@@ -117,6 +117,160 @@ int popc64(uint64_t x) { return __builtin_popcountll(x); }
 // local position of global qubit q in a stage with local mask lmask
 uint8_t local_pos(uint64_t lmask, int q) { return (uint8_t)popc64(lmask & ((1ull << q) - 1ull)); }
 
+// one op in a stage with local mask lm
+void emit_op(sv_batch_ctx *b, const QOp &qo, uint64_t lm) {
+    svk::BOp op{};
+    op.kind = (uint8_t)qo.kind;
+    op.k = (uint8_t)qo.t.size();
+    for (size_t i = 0; i < qo.t.size(); ++i) op.t[i] = local_pos(lm, qo.t[i]);
+    std::vector<int> ins;
+    if (qo.kind != svk::BOP_DIAG)
+        for (int q : qo.t) ins.push_back(local_pos(lm, q));
+    for (int q : qo.c) ins.push_back(local_pos(lm, q));
+    std::sort(ins.begin(), ins.end());
+    op.np = (uint8_t)ins.size();
+    for (size_t i = 0; i < ins.size(); ++i) op.p[i] = (uint8_t)ins[i];
+    op.cval = 0;
+    for (size_t i = 0; i < qo.c.size(); ++i)
+        if (qo.cv[i]) op.cval |= 1u << local_pos(lm, qo.c[i]);
+    op.mat = (uint32_t)b->pool.size();
+    const int D = 1 << op.k;
+    for (size_t i = 0; i < qo.data.size(); ++i) {
+        float2 v;
+        if (qo.kind == svk::BOP_PERM && (int)i >= D) {
+            const int dst = (int)qo.data[i].real();
+            std::memcpy(&v.x, &dst, 4);
+            v.y = 0.f;
+        } else {
+            v = make_float2((float)qo.data[i].real(), (float)qo.data[i].imag());
+        }
+        b->pool.push_back(v);
+    }
+    b->ops.push_back(op);
+}
+
+float2 bits_f2(uint32_t x, uint32_t y) {
+    float2 v;
+    std::memcpy(&v.x, &x, 4);
+    std::memcpy(&v.y, &y, 4);
+    return v;
+}
+
+// an op that a window can hold: at most 2 targets, all its qubits among <= w
+bool windowable(const QOp &qo, int w) {
+    if (popc64(qo.qmask) > w || qo.t.size() > 2) return false;
+    return qo.kind == svk::BOP_DENSE || qo.kind == svk::BOP_DIAG || qo.kind == svk::BOP_PERM;
+}
+
+// a window: the ops (at most 2 targets each, all on the local positions `wq`)
+// applied one after another to 2^|wq| amplitudes held in registers
+void emit_window(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vector<int> &idx, uint64_t wq,
+                 uint64_t lm) {
+    svk::BOp op{};
+    op.kind = svk::BOP_WIN;
+    op.k = (uint8_t)idx.size();
+    std::vector<int> wl;                    // window bit i <-> local position wl[i]
+    for (int q = 0; q < 64; ++q)
+        if ((wq >> q) & 1u) wl.push_back(local_pos(lm, q));
+    std::sort(wl.begin(), wl.end());
+    op.np = (uint8_t)wl.size();
+    for (size_t i = 0; i < wl.size(); ++i) op.p[i] = (uint8_t)wl[i];
+    op.cval = 0;
+    op.mat = (uint32_t)b->pool.size();
+    auto wbit = [&](int q) {
+        const int l = local_pos(lm, q);
+        return (int)(std::find(wl.begin(), wl.end(), l) - wl.begin());
+    };
+    const size_t hdr = b->pool.size();
+    b->pool.resize(hdr + 2 * idx.size());
+    for (size_t s = 0; s < idx.size(); ++s) {
+        const QOp &qo = qops[idx[s]];
+        uint32_t cm = 0, cv = 0;
+        for (size_t i = 0; i < qo.c.size(); ++i) {
+            cm |= 1u << wbit(qo.c[i]);
+            if (qo.cv[i]) cv |= 1u << wbit(qo.c[i]);
+        }
+        const int k = (int)qo.t.size(), D = 1 << k;
+        const int b0 = k > 0 ? wbit(qo.t[0]) : 0, b1 = k > 1 ? wbit(qo.t[1]) : 0;
+        const uint32_t moff = (uint32_t)(b->pool.size() - hdr);
+        uint32_t kind;
+        if (qo.kind == svk::BOP_DIAG) {
+            kind = svk::BSUB_DIAG;
+            for (int j = 0; j < D; ++j) b->pool.push_back(make_float2((float)qo.data[j].real(), (float)qo.data[j].imag()));
+        } else if (qo.kind == svk::BOP_PERM && k == 1) {
+            // the only non-diagonal one-target permutation: member l goes to 1 - l times f[l]
+            kind = svk::BSUB_SWAP1;
+            for (int l = 0; l < 2; ++l) b->pool.push_back(make_float2((float)qo.data[l].real(), (float)qo.data[l].imag()));
+        } else {
+            kind = k == 1 ? svk::BSUB_DENSE1 : svk::BSUB_DENSE2;
+            std::vector<cd> m(D * D, cd(0));
+            if (qo.kind == svk::BOP_PERM) {
+                for (int l = 0; l < D; ++l) m[(int)qo.data[D + l].real() * D + l] = qo.data[l];
+            } else {
+                m = qo.data;
+            }
+            for (int i = 0; i < D * D; ++i) b->pool.push_back(make_float2((float)m[i].real(), (float)m[i].imag()));
+        }
+        b->pool[hdr + 2 * s] = bits_f2(kind | (uint32_t)b0 << 8 | (uint32_t)b1 << 16 | (uint32_t)k << 24, cm | cv << 8);
+        b->pool[hdr + 2 * s + 1] = bits_f2(moff, 0);
+    }
+    b->ops.push_back(op);
+}
+
+// The ops of one stage, in order. With `windows`, runs of small ops go into
+// windows of at most kBatchWinQubits qubits -- fewer when the tile is small, so
+// that the 2^(T - w) amplitude groups still give every thread of the CTA work
+// -- chosen by the same commutation-aware greedy rule as gate fusion: an op
+// joins the window, at or after the last item touching its qubits, that grows
+// least while staying within the width.
+void emit_stage(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vector<int> &ids, uint64_t lm, int T,
+                bool windows) {
+    int wmax = std::min(svk::kBatchWinQubits, T - 9);
+    if (!windows || wmax < 2) {
+        for (int i : ids) emit_op(b, qops[i], lm);
+        return;
+    }
+    struct WItem { bool win; uint64_t q; std::vector<int> ops; };
+    std::vector<WItem> items;
+    std::vector<int> last(64, -1);
+    for (int i : ids) {
+        const QOp &qo = qops[i];
+        int L = -1;
+        for (int q = 0; q < 64; ++q)
+            if ((qo.qmask >> q) & 1u) L = std::max(L, last[q]);
+        if (qo.qmask == 0) L = (int)items.size() - 1;   // a global phase stays in place
+        int best = -1;
+        if (windowable(qo, wmax)) {
+            int best_growth = 1 << 30;
+            for (int j = std::max(L, 0); j < (int)items.size(); ++j) {
+                if (!items[j].win || items[j].ops.size() >= 64) continue;
+                const int growth = popc64(qo.qmask & ~items[j].q);
+                if (popc64(items[j].q | qo.qmask) <= wmax && growth < best_growth) {
+                    best = j;
+                    best_growth = growth;
+                }
+            }
+            if (best < 0) {
+                items.push_back({true, 0, {}});
+                best = (int)items.size() - 1;
+            }
+        } else {
+            items.push_back({false, 0, {}});
+            best = (int)items.size() - 1;
+        }
+        items[best].q |= qo.qmask;
+        items[best].ops.push_back(i);
+        for (int q = 0; q < 64; ++q)
+            if ((qo.qmask >> q) & 1u) last[q] = best;
+    }
+    for (const WItem &w : items) {
+        if (!w.win || w.ops.size() == 1 || w.q == 0)
+            for (int i : w.ops) emit_op(b, qops[i], lm);
+        else
+            emit_window(b, qops, w.ops, w.q, lm);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -229,36 +383,14 @@ SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, 
             svk::BStage bs{};
             bs.lmask = lm;
             bs.op_begin = (int)b->ops.size();
-            for (int oidx : st.ops) {
-                const QOp &qo = qops[oidx];
-                svk::BOp op{};
-                op.kind = (uint8_t)qo.kind;
-                op.k = (uint8_t)qo.t.size();
-                for (size_t i = 0; i < qo.t.size(); ++i) op.t[i] = local_pos(lm, qo.t[i]);
-                std::vector<int> ins;
-                if (qo.kind != svk::BOP_DIAG)
-                    for (int q : qo.t) ins.push_back(local_pos(lm, q));
-                for (int q : qo.c) ins.push_back(local_pos(lm, q));
-                std::sort(ins.begin(), ins.end());
-                op.np = (uint8_t)ins.size();
-                for (size_t i = 0; i < ins.size(); ++i) op.p[i] = (uint8_t)ins[i];
-                op.cval = 0;
-                for (size_t i = 0; i < qo.c.size(); ++i)
-                    if (qo.cv[i]) op.cval |= 1u << local_pos(lm, qo.c[i]);
-                op.mat = (uint32_t)b->pool.size();
-                const int D = 1 << op.k;
-                for (size_t i = 0; i < qo.data.size(); ++i) {
-                    float2 v;
-                    if (qo.kind == svk::BOP_PERM && (int)i >= D) {
-                        const int dst = (int)qo.data[i].real();
-                        std::memcpy(&v.x, &dst, 4);
-                        v.y = 0.f;
-                    } else {
-                        v = make_float2((float)qo.data[i].real(), (float)qo.data[i].imag());
-                    }
-                    b->pool.push_back(v);
-                }
-                b->ops.push_back(op);
+            const size_t pool0 = b->pool.size(), ops0 = b->ops.size();
+            // windows need the stage's matrices staged in shared memory; if they would
+            // not fit, the stage is emitted again op by op
+            emit_stage(b, qops, st.ops, lm, T, true);
+            if ((int)(b->pool.size() - pool0) > svk::kBatchStageMat) {
+                b->pool.resize(pool0);
+                b->ops.resize(ops0);
+                emit_stage(b, qops, st.ops, lm, T, false);
             }
             bs.op_end = (int)b->ops.size();
             bs.pool_begin = bs.op_end > bs.op_begin ? (int)b->ops[bs.op_begin].mat : (int)b->pool.size();

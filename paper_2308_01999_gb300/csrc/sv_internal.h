@@ -101,7 +101,14 @@ cudaError_t launch_wait_probe(const LaunchCtx &L, int *d_err, long long cycles);
 // applies all of them.
 constexpr int kBatchTileQubits = 14;
 constexpr int kBatchThreads = 512;
-enum BatchOpKind { BOP_DENSE = 0, BOP_DIAG = 1, BOP_PERM = 2 };
+enum BatchOpKind { BOP_DENSE = 0, BOP_DIAG = 1, BOP_PERM = 2, BOP_WIN = 3 };
+// A window (BOP_WIN) applies a run of small ops to amplitudes held in registers:
+// its np <= kBatchWinQubits local positions p[] span 2^np amplitudes per thread,
+// k is the number of sub-ops, and pool[mat ..] holds k two-entry headers
+// (kind | b0 << 8 | b1 << 16 | nd << 24, control mask | control values << 8,
+// matrix offset from pool[mat], 0) followed by their matrices.
+constexpr int kBatchWinQubits = 4;
+enum BatchSubKind { BSUB_DENSE1 = 0, BSUB_DENSE2 = 1, BSUB_DIAG = 2, BSUB_SWAP1 = 3 };
 
 struct BItem {
     uint64_t state_off;      // amplitude offset of the state

@@ -49,6 +49,13 @@ def test_compile_on_host_only(svmod):
     one = sv.Batch()
     assert one.compile(states[:3], 3)["stages"] == 3
     assert info["stages"] > 5
+    # runs of small ops on at most 4 qubits become register windows: a 14-qubit
+    # ansatz compiled without fusion needs far fewer ops than it has gates
+    rng = gen.rng_for(5)
+    ans = gen.ansatz_circuit(14, 3, rng)
+    w = sv.Batch()
+    assert w.compile([(14, ans, np.zeros((0, 14)))], 1)["ops"] < len(ans) / 3
+    w.close()
     with pytest.raises(sv.SvError):
         sv.Batch().compile([(3, [gen.Gate((3,), np.eye(2))], np.zeros((0, 3)))], 2)
     with pytest.raises(sv.SvError):
