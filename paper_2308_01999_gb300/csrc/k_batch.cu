@@ -30,6 +30,14 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(__fmaf_rn(a.x, b.x, -a.y * b.y), __fmaf_rn(a.x, b.y, a.y * b.x));
 }
 
+// Shared-memory layout of the tile: amplitude a sits at a ^ ((a >> 4) & 15). A
+// group's members differ in the op's target bits only, so without the swizzle
+// the 32 lanes of a warp (consecutive groups) read member j of groups whose
+// low four bits agree whenever the targets cover bits 0..3 -- all in one bank
+// pair. Mixing bits 4..7 into the bank index spreads them; runs of consecutive
+// amplitudes stay conflict free (each half-warp XORs one constant).
+__device__ __forceinline__ uint32_t sw(uint32_t a) { return a ^ ((a >> 4) & 15u); }
+
 __device__ __forceinline__ uint32_t insert_zeros_local(uint32_t g, const BOp &op) {
 #pragma unroll 1
     for (int i = 0; i < op.np; ++i) {
@@ -66,7 +74,7 @@ __device__ void op_dense(float2 *tile, const BOp &op, const float2 *msh, int T) 
         const uint32_t base = insert_zeros_local((uint32_t)g, op);
         float2 v[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) v[j] = tile[base | off[j]];
+        for (int j = 0; j < D; ++j) v[j] = tile[sw(base | off[j])];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             float2 acc = make_float2(0.f, 0.f);
@@ -78,7 +86,7 @@ __device__ void op_dense(float2 *tile, const BOp &op, const float2 *msh, int T) 
                 acc.y = __fmaf_rn(m.x, v[l].y, acc.y);
                 acc.y = __fmaf_rn(m.y, v[l].x, acc.y);
             }
-            tile[base | off[j]] = acc;
+            tile[sw(base | off[j])] = acc;
         }
     }
 }
@@ -98,9 +106,9 @@ __device__ void op_perm(float2 *tile, const BOp &op, const float2 *msh, int T) {
         const uint32_t base = insert_zeros_local((uint32_t)g, op);
         float2 v[D];
 #pragma unroll
-        for (int l = 0; l < D; ++l) v[l] = tile[base | src[l]];
+        for (int l = 0; l < D; ++l) v[l] = tile[sw(base | src[l])];
 #pragma unroll
-        for (int l = 0; l < D; ++l) tile[base | dst[l]] = cmulf(msh[l], v[l]);
+        for (int l = 0; l < D; ++l) tile[sw(base | dst[l])] = cmulf(msh[l], v[l]);
     }
 }
 
@@ -111,7 +119,7 @@ __device__ void op_diag(float2 *tile, const BOp &op, const float2 *msh, int T) {
         const uint32_t a = insert_zeros_local((uint32_t)g, op);
         int j = 0;
         for (int t = 0; t < op.k; ++t) j |= (int)((a >> op.t[t]) & 1u) << t;
-        tile[a] = cmulf(msh[j], tile[a]);
+        tile[sw(a)] = cmulf(msh[j], tile[sw(a)]);
     }
 }
 
@@ -209,7 +217,7 @@ __device__ void op_window(float2 *tile, const BOp &op, const float2 *blk, int T)
         const uint32_t base = insert_zeros_local((uint32_t)g, op);
         float2 v[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) v[j] = tile[base | off[j]];
+        for (int j = 0; j < D; ++j) v[j] = tile[sw(base | off[j])];
         for (int s = 0; s < nsub; ++s) {
             const float2 h0 = blk[2 * s], h1 = blk[2 * s + 1];
             const uint32_t hx = __float_as_uint(h0.x), hy = __float_as_uint(h0.y);
@@ -244,7 +252,7 @@ __device__ void op_window(float2 *tile, const BOp &op, const float2 *blk, int T)
             }
         }
 #pragma unroll
-        for (int j = 0; j < D; ++j) tile[base | off[j]] = v[j];
+        for (int j = 0; j < D; ++j) tile[sw(base | off[j])] = v[j];
     }
 }
 
@@ -314,9 +322,9 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
                 }
                 if (st == it.stage_begin) {
                     for (int l = threadIdx.x; l < L; l += kT)
-                        tile[l] = make_float2((tbase | lo_tab[l & 127] | hi_tab[l >> 7]) == 0u ? 1.f : 0.f, 0.f);
+                        tile[sw(l)] = make_float2((tbase | lo_tab[l & 127] | hi_tab[l >> 7]) == 0u ? 1.f : 0.f, 0.f);
                 } else {
-                    for (int l = threadIdx.x; l < L; l += kT) tile[l] = sv[tbase | lo_tab[l & 127] | hi_tab[l >> 7]];
+                    for (int l = threadIdx.x; l < L; l += kT) tile[sw(l)] = sv[tbase | lo_tab[l & 127] | hi_tab[l >> 7]];
                 }
                 for (int o = S.op_begin; o < S.op_end; ++o) {
                     const BOp op = ops[o];
@@ -359,7 +367,7 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
                 }
                 __syncthreads();
                 if (n > T || keep_states)
-                    for (int l = threadIdx.x; l < L; l += kT) sv[tbase | lo_tab[l & 127] | hi_tab[l >> 7]] = tile[l];
+                    for (int l = threadIdx.x; l < L; l += kT) sv[tbase | lo_tab[l & 127] | hi_tab[l >> 7]] = tile[sw(l)];
                 __syncthreads();
             }
         }
@@ -378,8 +386,8 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
             for (uint32_t g = threadIdx.x; g < npairs; g += kT) {
                 const uint32_t i = x ? (((g >> pb) << (pb + 1)) | (g & ((1u << pb) - 1u))) : g;
                 const uint32_t j = i ^ x;
-                const float2 a = n == T ? tile[i] : sv[i];
-                const float2 b = x ? (n == T ? tile[j] : sv[j]) : a;
+                const float2 a = n == T ? tile[sw(i)] : sv[i];
+                const float2 b = x ? (n == T ? tile[sw(j)] : sv[j]) : a;
                 const float re = a.x * b.x + a.y * b.y, im = a.y * b.x - a.x * b.y;
                 const float ti = P.use_im ? im : re;
                 run += (__popc(i & z) & 1) ? -ti : ti;

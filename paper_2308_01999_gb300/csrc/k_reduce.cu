@@ -13,15 +13,16 @@
 // unit i ^ x so that both partners come from the same two loads.
 //
 // Precision. Terms are formed in the state's precision. For complex64 each
-// thread sums the terms of one loop iteration in FP32 (at most 16 terms per
-// string: 4 work items x 2 units x 2 amplitudes), so that partial carries a
-// relative rounding error of at most 16 u (u = 2^-24) of the sum of its terms'
-// magnitudes; partials are then summed in FP64 across iterations, threads and
-// blocks. Since sum_i |w_i| <= <psi|psi>, the absolute error of a complex64
-// expectation value is at most about 1e-6 <psi|psi> (typically far less).
-// complex128 uses FP64 throughout. Block partials are reduced by a
-// second kernel in a fixed order, so results are bitwise reproducible for a
-// given launch shape.
+// thread sums the terms of one loop iteration in FP32 (at most 8 per string:
+// 4 work items x 2 amplitudes), so that partial carries a relative rounding
+// error of at most 8 u (u = 2^-24) of the sum of its terms' magnitudes; the
+// partials are accumulated per thread in FP32 with compensation (error about
+// 2 u of the sum of magnitudes) and summed in FP64 across threads and blocks.
+// Since sum_i |w_i| <= <psi|psi> and a pair's term carries a factor 2, the
+// absolute error of a complex64 expectation value is at most about
+// 1.2e-6 <psi|psi> (typically far less). complex128 uses FP64 throughout.
+// Block partials are reduced by a second kernel in a fixed order, so results
+// are bitwise reproducible for a given launch shape.
 #include "sv_internal.h"
 
 namespace svk {
@@ -100,64 +101,95 @@ k_finish(const double *__restrict__ partials, int nblocks, int S, PauliPass P, i
     }
 }
 
-template <typename R>
+// Pauli pass kernel. Terms are enumerated once per unordered pair {i, i ^ x}:
+// with w = psi_i conj(psi_{i^x}) the pair contributes
+//   (-1)^{par(i & z)} [sel(w) + (-1)^{par(x & z)} sel(conj(w))]
+//     = (-1)^{par(i & z)} sel(w) (1 + (-1)^{par(x & z) + use_im}),
+// i.e. twice the first term or exactly zero; the host folds that factor (2 or
+// 0, and 1 when x = 0, where every i is its own partner and w = |psi_i|^2) into
+// the string's sign. Within a 16-byte unit the parities of the elements differ
+// from the unit's by the low bit of z, and the partner unit's by par(x & z),
+// so one 64-bit popcount per unit and string suffices.
+// MODE 0: x = 0. MODE 1: x = 1 (complex64 only: partners share a unit).
+// MODE 2: partners in units u and u ^ xu (pairs enumerated by inserting a zero
+// at xu's lowest bit). SM: strings per pass rounded up to 1, 2, 4 or 8.
+struct PauliK {
+    int S;
+    uint64_t zu[kPauliMaxS];     // z without its low unit-index bits
+    unsigned zl[kPauliMaxS];     // bit 0 of z (complex64: element parity inside a unit)
+    int use_im[kPauliMaxS];
+};
+
+// acc += x with the rounding error of each addition carried in c (Neumaier):
+// for complex64 the running sums stay in FP32 (GB300's FP64 rate is a small
+// fraction of its FP32 rate) at the accuracy of an FP64 accumulator of FP32 terms
+__device__ __forceinline__ void comp_add(float &acc, float &c, float x) {
+    const float t = acc + x;
+    c += fabsf(acc) >= fabsf(x) ? (acc - t) + x : (x - t) + acc;
+    acc = t;
+}
+
+template <typename R, int MODE, int SM>
 __global__ void __launch_bounds__(kThreads)
-k_pauli(const typename CT<R>::T *__restrict__ sv, uint64_t n_work, int pair_bit, uint64_t xu, unsigned xl,
-        PauliPass P, double *__restrict__ partials) {
+k_pauli(const typename CT<R>::T *__restrict__ sv, uint64_t n_work, int pair_bit, uint64_t xu, unsigned xl, PauliK P,
+        double *__restrict__ partials) {
     using C = typename CT<R>::T;
     constexpr int V = CT<R>::V;
-    double tot[kPauliMaxS];
-    R run[kPauliMaxS];
+    R acc[SM], cmp[SM];
 #pragma unroll
-    for (int s = 0; s < kPauliMaxS; ++s) { tot[s] = 0.0; run[s] = R(0); }
-    auto add = [&](uint64_t i, const C &w) {
-#pragma unroll
-        for (int s = 0; s < kPauliMaxS; ++s) {
-            if (s < P.S) {
-                const R t = P.use_im[s] ? w.y : w.x;
-                run[s] += (__popcll(i & P.z[s]) & 1) ? -t : t;
-            }
-        }
-    };
+    for (int s = 0; s < SM; ++s) { acc[s] = R(0); cmp[s] = R(0); }
     const uint64_t stride = (uint64_t)gridDim.x * kThreads * kIlp;
-    int iter = 0;
     for (uint64_t w0 = (uint64_t)blockIdx.x * kThreads * kIlp + threadIdx.x; w0 < n_work; w0 += stride) {
         C A[kIlp][V], B[kIlp][V];
-        uint64_t ua[kIlp], ub[kIlp];
+        uint64_t ua[kIlp];
 #pragma unroll
         for (int q = 0; q < kIlp; ++q) {
             const uint64_t w = w0 + (uint64_t)q * kThreads;
-            ua[q] = pair_bit < 0 ? w : insert_zero(w, pair_bit);
-            ub[q] = ua[q] ^ xu;
+            ua[q] = MODE == 2 ? insert_zero(w, pair_bit) : w;
             if (w < n_work) {
                 load_unit<R>(sv, ua[q], A[q]);
-                if (pair_bit >= 0) load_unit<R>(sv, ub[q], B[q]);
+                if constexpr (MODE == 2) load_unit<R>(sv, ua[q] ^ xu, B[q]);
             }
         }
+        R run[SM];
+#pragma unroll
+        for (int s = 0; s < SM; ++s) run[s] = R(0);
 #pragma unroll
         for (int q = 0; q < kIlp; ++q) {
             if (w0 + (uint64_t)q * kThreads >= n_work) continue;
-            if (pair_bit < 0) {
+            // terms of this work item: element e's value t[e] (re, im) and its parity offset
+            C t[V];
+            if constexpr (MODE == 0) {
 #pragma unroll
-                for (int e = 0; e < V; ++e) add(ua[q] * V + e, mul_conj(A[q][e], xl ? A[q][V - 1 - e] : A[q][e]));
+                for (int e = 0; e < V; ++e) t[e] = C{A[q][e].x * A[q][e].x + A[q][e].y * A[q][e].y, R(0)};
+            } else if constexpr (MODE == 1) {
+                t[0] = mul_conj(A[q][0], A[q][V - 1]);
             } else {
 #pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    // partner of element e is element e ^ xl of the other unit (xl is 0 or 1)
-                    add(ua[q] * V + e, mul_conj(A[q][e], xl ? B[q][V - 1 - e] : B[q][e]));
-                    add(ub[q] * V + e, mul_conj(B[q][e], xl ? A[q][V - 1 - e] : A[q][e]));
+                for (int e = 0; e < V; ++e) t[e] = mul_conj(A[q][e], xl ? B[q][V - 1 - e] : B[q][e]);
+            }
+#pragma unroll
+            for (int s = 0; s < SM; ++s) {
+                if (s >= P.S) continue;
+                const unsigned p0 = (unsigned)__popcll(ua[q] & P.zu[s]) & 1u;
+#pragma unroll
+                for (int e = 0; e < (MODE == 1 ? 1 : V); ++e) {
+                    const R v = P.use_im[s] ? t[e].y : t[e].x;
+                    run[s] += (p0 ^ ((unsigned)e & P.zl[s])) ? -v : v;
                 }
             }
         }
-        if (++iter == kRun) {
 #pragma unroll
-            for (int s = 0; s < kPauliMaxS; ++s) { tot[s] += (double)run[s]; run[s] = R(0); }
-            iter = 0;
+        for (int s = 0; s < SM; ++s) {
+            if (s >= P.S) continue;
+            if constexpr (sizeof(R) == 4) comp_add(acc[s], cmp[s], run[s]);
+            else acc[s] += run[s];
         }
     }
+    double tot[SM];
 #pragma unroll
-    for (int s = 0; s < kPauliMaxS; ++s) tot[s] += (double)run[s];
-    block_reduce_store<kPauliMaxS>(tot, P.S, partials + (size_t)blockIdx.x * 8);
+    for (int s = 0; s < SM; ++s) tot[s] = (double)acc[s] + (double)cmp[s];
+    block_reduce_store<SM>(tot, P.S, partials + (size_t)blockIdx.x * 8);
 }
 
 template <typename R>
@@ -231,28 +263,50 @@ inline int reduce_grid(const LaunchCtx &L, uint64_t work, int max_blocks) {
     return (int)(b == 0 ? 1 : b);
 }
 
+template <typename R, int MODE>
+cudaError_t pauli_launch(const LaunchCtx &L, const typename CT<R>::T *sv, int grid, uint64_t n_work, int pair_bit,
+                         uint64_t xu, unsigned xl, const PauliK &K, double *d_partials) {
+    const int S = K.S;
+    if (S <= 1) k_pauli<R, MODE, 1><<<grid, kThreads, 0, L.stream>>>(sv, n_work, pair_bit, xu, xl, K, d_partials);
+    else if (S <= 2) k_pauli<R, MODE, 2><<<grid, kThreads, 0, L.stream>>>(sv, n_work, pair_bit, xu, xl, K, d_partials);
+    else if (S <= 4) k_pauli<R, MODE, 4><<<grid, kThreads, 0, L.stream>>>(sv, n_work, pair_bit, xu, xl, K, d_partials);
+    else k_pauli<R, MODE, 8><<<grid, kThreads, 0, L.stream>>>(sv, n_work, pair_bit, xu, xl, K, d_partials);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t pauli_t(const LaunchCtx &L, const void *sv, int n, const PauliPass &P, double *d_partials, int maxb,
                     double *d_out) {
     using C = typename CT<R>::T;
     constexpr int V = CT<R>::V;
+    if (P.S < 1 || P.S > kPauliMaxS) return cudaErrorInvalidValue;
     const int vb = V == 2 ? 1 : 0;                   // log2 V
     const uint64_t n_units = (1ull << n) >> vb;
     const unsigned xl = (unsigned)(P.x & (V - 1));
     const uint64_t xu = P.x >> vb;
-    int pair_bit = -1;
-    uint64_t n_work = n_units;
-    if (xu != 0) {
-        pair_bit = __builtin_ctzll(xu);
-        n_work = n_units / 2;
+    const int mode = P.x == 0 ? 0 : (xu == 0 ? 1 : 2);
+    PauliK K{};
+    K.S = P.S;
+    PauliPass Pf = P;                                 // signs with the pair factor folded in
+    for (int s = 0; s < P.S; ++s) {
+        K.zu[s] = P.z[s] >> vb;
+        K.zl[s] = (unsigned)(P.z[s] & (V - 1));
+        K.use_im[s] = P.use_im[s];
+        const int pxz = __builtin_popcountll(P.x & P.z[s]) & 1;
+        Pf.sign[s] = mode == 0 ? P.sign[s] : (pxz == (P.use_im[s] ? 1 : 0) ? 2.0 * P.sign[s] : 0.0);
     }
+    const uint64_t n_work = mode == 2 ? n_units / 2 : n_units;
+    const int pair_bit = mode == 2 ? __builtin_ctzll(xu) : -1;
     const int grid = reduce_grid(L, n_work, maxb);
-    k_pauli<R><<<grid, kThreads, 0, L.stream>>>(reinterpret_cast<const C *>(sv), n_work, pair_bit, xu, xl, P,
-                                                d_partials);
-    ++*L.launches;
-    cudaError_t e = cudaGetLastError();
+    const C *s = reinterpret_cast<const C *>(sv);
+    cudaError_t e;
+    if (mode == 0) e = pauli_launch<R, 0>(L, s, grid, n_work, pair_bit, xu, xl, K, d_partials);
+    else if (mode == 2) e = pauli_launch<R, 2>(L, s, grid, n_work, pair_bit, xu, xl, K, d_partials);
+    else if constexpr (V == 2) e = pauli_launch<R, 1>(L, s, grid, n_work, pair_bit, xu, xl, K, d_partials);
+    else return cudaErrorInvalidValue;
     if (e != cudaSuccess) return e;
-    k_finish<<<1, kThreads, 0, L.stream>>>(d_partials, grid, P.S, P, 1, d_out);
+    k_finish<<<1, kThreads, 0, L.stream>>>(d_partials, grid, P.S, Pf, 1, d_out);
     ++*L.launches;
     return cudaGetLastError();
 }
