@@ -380,8 +380,9 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
             float run = 0.f;
             int cnt = 0;
             // terms i and i ^ x come from the same pair of loads: w_i = psi_i conj(psi_{i^x}),
-            // w_{i^x} = conj(w_i); pairs are enumerated by clearing the lowest bit of x
-            const int pb = x ? __ffs(x) - 1 : 0;
+            // w_{i^x} = conj(w_i); pairs are enumerated by inserting a zero at the highest
+            // bit of x (any set bit would do; the highest keeps a warp's loads contiguous)
+            const int pb = x ? 31 - __clz(x) : 0;
             const uint32_t npairs = x ? N / 2 : N;
             for (uint32_t g = threadIdx.x; g < npairs; g += kT) {
                 const uint32_t i = x ? (((g >> pb) << (pb + 1)) | (g & ((1u << pb) - 1u))) : g;

@@ -626,7 +626,9 @@ cudaError_t pauli_rot_t(const LaunchCtx &L, void *sv, int n, uint64_t x, uint64_
     int pair_bit = -1;
     uint64_t n_work = n_units;
     if (xu != 0) {
-        pair_bit = __builtin_ctzll(xu);
+        // pairs {u, u ^ xu}: a zero inserted at xu's highest set bit (any set bit
+        // enumerates each pair once; the highest keeps warp accesses contiguous)
+        pair_bit = 63 - __builtin_clzll(xu);
         n_work = n_units / 2;
     }
     uint64_t grid = (n_work + kThreads - 1) / kThreads;

@@ -112,7 +112,7 @@ k_finish(const double *__restrict__ partials, int nblocks, int S, PauliPass P, i
 // so one 64-bit popcount per unit and string suffices.
 // MODE 0: x = 0. MODE 1: x = 1 (complex64 only: partners share a unit).
 // MODE 2: partners in units u and u ^ xu (pairs enumerated by inserting a zero
-// at xu's lowest bit). SM: strings per pass rounded up to 1, 2, 4 or 8.
+// at xu's highest bit). SM: strings per pass rounded up to 1, 2, 4 or 8.
 struct PauliK {
     int S;
     uint64_t zu[kPauliMaxS];     // z without its low unit-index bits
@@ -297,7 +297,9 @@ cudaError_t pauli_t(const LaunchCtx &L, const void *sv, int n, const PauliPass &
         Pf.sign[s] = mode == 0 ? P.sign[s] : (pxz == (P.use_im[s] ? 1 : 0) ? 2.0 * P.sign[s] : 0.0);
     }
     const uint64_t n_work = mode == 2 ? n_units / 2 : n_units;
-    const int pair_bit = mode == 2 ? __builtin_ctzll(xu) : -1;
+    // pairs {u, u ^ xu} are enumerated by inserting a zero at one set bit of xu;
+    // any set bit works, and the highest keeps each warp's loads in 512-byte runs
+    const int pair_bit = mode == 2 ? 63 - __builtin_clzll(xu) : -1;
     const int grid = reduce_grid(L, n_work, maxb);
     const C *s = reinterpret_cast<const C *>(sv);
     cudaError_t e;
