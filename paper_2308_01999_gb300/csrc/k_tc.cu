@@ -526,7 +526,7 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-// ---------------- raw-operand variant (TF32, qubit 0 not a target) ----------------
+// ---------------- raw-operand variant (TF32 or split BF16, qubit 0 not a target) ----------------
 // The same product written with the member index as the contraction:
 //   D(128 x 256) = A(128 x 64) * B(64 x 256),  B[l][2i + f] = component f of
 //   amplitude (member l, column i),  A row m = 32q + r: member j = 16q + r % 16,
@@ -534,25 +534,28 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
 // so D holds (Re G) x and (Im G) x for the re and im parts of x, and
 //   out_j = (Re G x_re - Im G x_im, Re G x_im + Im G x_re)
 // combines two rows that sit 16 TMEM lanes apart in the same warp's quarter.
-// B in shared memory is the state itself, MN-major (columns contiguous) in the
-// 128-byte swizzle with 32-byte atomicity, the swizzle tf32 MMA takes for
-// MN-major operands (with the plain 128-byte swizzle it produced no result on
-// GB300): each 16-byte chunk is two adjacent amplitudes of one member. Roles
-// (15 warps): 2 copy warps issue cp.async.cg (no registers, no L1 allocation)
-// and let the copies arrive on the stage's `landed` barrier, so they never wait
-// for data; 4 round warps round the landed stage to TF32 in place (the tensor
-// core drops the low 13 bits, which measured as a norm drift of -3.5e-4 per gate
-// unrounded); one thread issues the MMAs; 8 epilogue warps combine, write the
-// tile's result into the stage it came from and store it back in runs of
-// columns. Three stages rotate. Needs qubit 0 free (a chunk is two adjacent
-// amplitudes); the launcher uses it from lowest target 2 up. Needs qubit 0 free (a chunk is two adjacent amplitudes); the
-// launcher uses it from lowest target 3 up.
+// B in shared memory is the state itself, MN-major (columns contiguous): a stage
+// is 64 atoms of 1 KiB, atom (a, g) = columns-floats 32a .. 32a+31 of members
+// 8g .. 8g+7 at a * 8192 + g * 1024, each in the 128-byte swizzle with 32-byte
+// atomicity (the swizzle tf32 MMA takes for MN-major operands; with the plain
+// 128-byte swizzle it produced no result on GB300). Each 16-byte chunk is two
+// adjacent amplitudes of one member. Roles (15 warps): 2 copy warps issue
+// cp.async.cg (no registers, no L1 allocation) and let the copies arrive on the
+// stage's `landed` barrier, so they never wait for data; 4 convert warps prepare
+// the landed stage in place -- TF32: round to nearest (the tensor core drops the
+// low 13 bits, which measured as a norm drift of -3.5e-4 per gate unrounded);
+// split BF16: each warp turns one 1 KiB atom into a 512-byte hi atom and a
+// 512-byte lo atom (x = hi + lo, both BF16, 64-byte swizzle) in the same 1 KiB;
+// one thread issues the MMAs (TF32: 8 of K = 8; BF16: Ahi Bhi + Ahi Blo + Alo Bhi
+// for 4 steps of K = 16); 8 epilogue warps combine, write the tile's result into
+// the stage it came from and store it back in runs of columns. Three stages
+// rotate. Needs qubit 0 free (a chunk is two adjacent amplitudes).
 constexpr int kNT3 = 128;                     // columns per tile (MMA N = 2 * kNT3 reals)
 constexpr int kStages3 = 3;
-constexpr int kA3 = 128 * 64 * 4;             // A image: 128 rows x 64 tf32, K-major
+constexpr int kA3 = 128 * 64 * 4;             // A image: 128 rows x 64 tf32 (or BF16 hi + lo), K-major
 constexpr int kB3 = 64 * 2 * kNT3 * 4;        // one stage: 64 members x 256 floats
 constexpr int kCopyWarps3 = 2;                // warps 0-1: cp.async issue
-constexpr int kRoundWarps3 = 4;               // warps 2-5: TF32 rounding in place
+constexpr int kRoundWarps3 = 4;               // warps 2-5: TF32 rounding / BF16 split in place
 constexpr int kProdWarps3 = kCopyWarps3 + kRoundWarps3;
 constexpr int kEpiWarps3 = 8;                 // warps 6-13
 constexpr int kMmaWarp3 = kProdWarps3 + kEpiWarps3;
@@ -569,38 +572,68 @@ constexpr int kGuard3 = 2048;              // unused bytes after the last stage
 constexpr int kSmem3 = kA3 + kStages3 * kB3 + kGuard3 + (int)sizeof(TcCtl3);
 
 // byte offset of the 16-byte chunk holding floats 4c .. 4c+3 of member row l
-// (c = amplitude pair, 0..63) in a stage. MN-major TF32 operands use the 128-byte
-// swizzle with 32-byte atomicity: rows of 128 bytes (32 floats of one member),
-// whose four 32-byte units are permuted by the row index mod 4; atoms along the
-// columns 1024 bytes apart, member groups of 8 rows 8192 bytes apart.
+// (c = amplitude pair, 0..63) in a stage: atom (c / 8, l / 8); inside it rows of
+// 128 bytes (32 floats of one member) whose four 32-byte units are permuted by
+// the row index mod 4
 __device__ __forceinline__ uint32_t mn_chunk(int l, int c) {
-    return (uint32_t)((l >> 3) * 8192 + (c >> 3) * 1024 + (l & 7) * 128 + ((((c & 7) >> 1) ^ (l & 3)) << 5) +
+    return (uint32_t)((c >> 3) * 8192 + (l >> 3) * 1024 + (l & 7) * 128 + ((((c & 7) >> 1) ^ (l & 3)) << 5) +
                       ((c & 1) << 4));
 }
 
-// MN-major operand descriptor (128-byte swizzle, 32-byte atomicity): column atoms
-// 1024 bytes apart (leading offset); the rows of an 8-row member group are
-// contiguous, so the stride offset (512 bytes, four rows) reads them in place
-__device__ __forceinline__ uint64_t sdesc_mn(uint32_t addr) {
+// MN-major operand descriptor: column atoms 8192 bytes apart (leading offset),
+// 8-row member groups `sbo` bytes apart, swizzle `mode` (1: 128 bytes with
+// 32-byte atomicity, 4: 64 bytes). Either reading of the two offsets stays
+// inside the stage and its guard.
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t addr, uint32_t sbo, uint32_t mode) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(1024u >> 4) << 16;
-    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)(8192u >> 4) << 16;
+    d |= (uint64_t)(sbo >> 4) << 32;
     d |= 1ull << 46;
-    d |= 1ull << 61;
+    d |= (uint64_t)mode << 61;
     return d;
 }
 
-// D = F32, A = B = TF32, A K-major, B MN-major (bit 16), N = 256, M = 128
+// D = F32, A = B = TF32 (2) or BF16 (1), A K-major, B MN-major (bit 16), N = 256, M = 128
+template <int P>
 __host__ __device__ constexpr uint32_t idesc3() {
-    return (1u << 4) | (2u << 7) | (2u << 10) | (1u << 16) | ((uint32_t)((2 * kNT3) >> 3) << 17) |
-           ((uint32_t)(128 >> 4) << 24);
+    return (1u << 4) | ((P == TF32 ? 2u : 1u) << 7) | ((P == TF32 ? 2u : 1u) << 10) | (1u << 16) |
+           ((uint32_t)((2 * kNT3) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// split BF16: one warp turns the 1 KiB atom at `atom` (8 rows x 32 floats, 128-byte
+// swizzle with 32-byte atomicity) into hi / lo atoms of 8 rows x 32 BF16 (64-byte
+// swizzle: 16-byte chunk c of row r at r * 64 + ((c ^ (r / 2 % 4)) << 4)) at atom
+// and atom + 512. Every lane reads its 32 bytes before any lane writes.
+__device__ __forceinline__ void split_atom(uint32_t atom, int lane) {
+    const int r = lane >> 2, u = lane & 3;          // row, physical 32-byte unit
+    const int lu = u ^ (r & 3);                     // logical unit: floats 8 lu .. 8 lu + 7
+    float x[8];
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3])
+                 : "r"(atom + (uint32_t)(r * 128 + u * 32)));
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
+                 : "r"(atom + (uint32_t)(r * 128 + u * 32 + 16)));
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) split_bf16(x[2 * k], x[2 * k + 1], hi[k], lo[k]);
+    __syncwarp();
+    const uint32_t o = (uint32_t)(r * 64 + ((lu ^ ((r >> 1) & 3)) << 4));
+    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(atom + o), "r"(hi[0]), "r"(hi[1]), "r"(hi[2]),
+                 "r"(hi[3])
+                 : "memory");
+    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(atom + 512u + o), "r"(lo[0]), "r"(lo[1]), "r"(lo[2]),
+                 "r"(lo[3])
+                 : "memory");
+    __syncwarp();
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
+template <int P>
 __global__ void __launch_bounds__(kThreads3, 1)
 k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *__restrict__ d_err) {
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
@@ -667,25 +700,31 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
         // every copy this thread issued has landed before the CTA may exit
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp < kProdWarps3) {
-        // ---------------- round: TF32 round-to-nearest in place ----------------
-        // The tensor core reads a TF32 operand as the float's top 19 bits; adding half of
-        // their last place (0x1000) to the bit pattern first makes that truncation a
-        // rounding to nearest, ties away from zero (what cvt.rna.tf32.f32 computes),
-        // for one integer add per value.
+        // ---------------- convert: TF32 rounding or BF16 split, in place ----------------
+        // TF32: the tensor core reads a TF32 operand as the float's top 19 bits; adding
+        // half of their last place (0x1000) to the bit pattern first makes that
+        // truncation a rounding to nearest, ties away from zero (what cvt.rna.tf32.f32
+        // computes), for one integer add per value.
         const int rt = threadIdx.x - kCopyWarps3 * 32;   // 0..127: pair rt & 63, members 2r + rt / 64
+        const int rw = rt >> 5;                          // convert warp 0..3: BF16 atoms 16 rw .. 16 rw + 15
         int i = 0;
         for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
             const int s = i % kStages3;
             if (!mbar_wait(smem_u32(&S.landed[s]), (i / kStages3) & 1, abort_flag, d_err)) break;
             const uint32_t sb = sB0 + (uint32_t)(s * kB3);
+            if constexpr (P == TF32) {
 #pragma unroll 8
-            for (int r = 0; r < 32; ++r) {
-                const uint32_t a = sb + mn_chunk(2 * r + (rt >> 6), rt & 63);
-                uint32_t x, y, z, w;
-                asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a));
-                asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(x + 0x1000u), "r"(y + 0x1000u),
-                             "r"(z + 0x1000u), "r"(w + 0x1000u)
-                             : "memory");
+                for (int r = 0; r < 32; ++r) {
+                    const uint32_t a = sb + mn_chunk(2 * r + (rt >> 6), rt & 63);
+                    uint32_t x, y, z, w;
+                    asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a));
+                    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(x + 0x1000u), "r"(y + 0x1000u),
+                                 "r"(z + 0x1000u), "r"(w + 0x1000u)
+                                 : "memory");
+                }
+            } else {
+#pragma unroll 4
+                for (int k = 0; k < 16; ++k) split_atom(sb + (uint32_t)((16 * rw + k) * 1024), lane);
             }
             fence_proxy_async();
             mbar_arrive(smem_u32(&S.full[s]));
@@ -702,17 +741,38 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(a * 2 * kNT3);
                 const uint32_t b_addr = sB0 + (uint32_t)(s * kB3);
-                // K = 64 members in 8 steps of 8: A K-block ks / 4 (16 KB apart), 32 bytes
-                // per step within its rows; B member group ks (8192 bytes apart)
+                if constexpr (P == TF32) {
+                    // K = 64 members in 8 steps of 8: A K-block ks / 4 (16 KB apart), 32 bytes
+                    // per step within its rows; B member group ks (1024 bytes apart)
 #pragma unroll
-                for (int ks = 0; ks < 8; ++ks) {
-                    const uint64_t ad = sdesc(a_addr + (uint32_t)((ks >> 2) * 16384 + (ks & 3) * 32));
-                    const uint64_t bd = sdesc_mn(b_addr + (uint32_t)(ks * 8192));
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-                        "l"(ad), "l"(bd), "r"(idesc3()), "r"(ks)
-                        : "memory");
+                    for (int ks = 0; ks < 8; ++ks) {
+                        const uint64_t ad = sdesc(a_addr + (uint32_t)((ks >> 2) * 16384 + (ks & 3) * 32));
+                        const uint64_t bd = sdesc_mn(b_addr + (uint32_t)(ks * 1024), 512u, 1u);
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                            "l"(ad), "l"(bd), "r"(idesc3<TF32>()), "r"(ks)
+                            : "memory");
+                    }
+                } else {
+                    // K = 64 members in 4 steps of 16 (A: 32 bytes per step within its 128-byte
+                    // rows, lo image 16 KB on; B: member groups 2 ks, 2 ks + 1, lo atoms 512
+                    // bytes on): Ahi Bhi + Ahi Blo + Alo Bhi
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t ah = sdesc(a_addr + (uint32_t)(ks * 32));
+                        const uint64_t al = sdesc(a_addr + 16384u + (uint32_t)(ks * 32));
+                        const uint64_t bh = sdesc_mn(b_addr + (uint32_t)(ks * 2048), 1024u, 4u);
+                        const uint64_t bl = sdesc_mn(b_addr + (uint32_t)(ks * 2048 + 512), 1024u, 4u);
+                        const uint64_t av[3] = {ah, ah, al}, bv[3] = {bh, bl, bh};
+#pragma unroll
+                        for (int x = 0; x < 3; ++x)
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                                "l"(av[x]), "l"(bv[x]), "r"(idesc3<BF16>()), "r"(ks + x)
+                                : "memory");
+                    }
                 }
                 mma_commit(smem_u32(&S.acc_full[a]));
             }
@@ -865,25 +925,37 @@ std::vector<unsigned char> build_a_image(const double *g, sv_precision_t prec) {
 }
 
 // A image of the raw-operand variant: row m = 32q + r holds Re G[16q + r % 16][.]
-// (r < 16) or Im G[16q + r % 16][.] (r >= 16); K = 64 members, two 128-byte K-blocks
-std::vector<unsigned char> build_a_image3(const double *g) {
+// (r < 16) or Im G[16q + r % 16][.] (r >= 16). TF32: K = 64 members in two
+// 128-byte K-blocks. Split BF16: hi and lo images (16 KB each) of one 128-byte
+// K-block each.
+std::vector<unsigned char> build_a_image3(const double *g, sv_precision_t prec) {
     std::vector<unsigned char> img(kA3, 0);
     for (int m = 0; m < 128; ++m) {
         const int j = 16 * (m >> 5) + (m & 15), part = (m >> 4) & 1;
         for (int k = 0; k < 64; ++k) {
-            const uint32_t w = host_tf32((float)g[2 * (j * 64 + k) + part]);
-            std::memcpy(&img[host_sw128(k >> 5, m, (k & 31) >> 2) + (k & 3) * 4], &w, 4);
+            const float x = (float)g[2 * (j * 64 + k) + part];
+            if (prec == SV_PREC_TF32) {
+                const uint32_t w = host_tf32(x);
+                std::memcpy(&img[host_sw128(k >> 5, m, (k & 31) >> 2) + (k & 3) * 4], &w, 4);
+            } else {
+                const uint16_t hi = host_bf16(x);
+                const uint16_t lo = host_bf16(x - bf16_to_float(hi));
+                const size_t o = host_sw128(0, m, k >> 3) + (k & 7) * 2;
+                std::memcpy(&img[o], &hi, 2);
+                std::memcpy(&img[16384 + o], &lo, 2);
+            }
         }
     }
     return img;
 }
 
+template <int P>
 cudaError_t run_tc_raw(const LaunchCtx &L, float2 *sv, const TcGeom &G, const uint4 *d_a, int *d_err) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc6_raw, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+    cudaError_t e = cudaFuncSetAttribute(k_tc6_raw<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
     if (e != cudaSuccess) return e;
     uint64_t grid = (uint64_t)L.num_sms;
     if (grid > G.n_tiles) grid = G.n_tiles;
-    k_tc6_raw<<<(unsigned)grid, kThreads3, kSmem3, L.stream>>>(sv, G, d_a, d_err);
+    k_tc6_raw<P><<<(unsigned)grid, kThreads3, kSmem3, L.stream>>>(sv, G, d_a, d_err);
     ++*L.launches;
     return cudaGetLastError();
 }
@@ -925,16 +997,16 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     G.n_tiles = (G.n_cols + kNT - 1) / kNT;
     float2 *s = reinterpret_cast<float2 *>(sv);
     const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
-    // TF32 with the lowest target at 2 or above (runs of at least 32 bytes): the
-    // raw-operand kernel, measured on GB300 at one time per block whatever the
-    // other targets (10.5 ms for a 32-qubit state when the lowest target is 4 or
-    // more, 11.9 ms at 3, 14.7 ms at 2). With the lowest target at 1 its 16-byte
-    // runs make it slower (18.5 ms) than the register-staged kernel below (16.4).
-    if (prec == SV_PREC_TF32 && tpos[0] >= kRawMinLowTarget && n >= 8) {
-        const std::vector<unsigned char> img = build_a_image3(mat);
+    // Lowest target 2 or above (runs of at least 32 bytes): the raw-operand kernel,
+    // measured on GB300 (TF32) at one time per block whatever the other targets
+    // (10.5 ms for a 32-qubit state when the lowest target is 4 or more, 11.9 ms at
+    // 3, 14.7 ms at 2). With the lowest target at 1 its 16-byte runs make it slower
+    // (18.5 ms) than the register-staged kernel below (16.4).
+    if (tpos[0] >= kRawMinLowTarget && n >= 8) {
+        const std::vector<unsigned char> img = build_a_image3(mat, prec);
         cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
         if (e != cudaSuccess) return e;
-        return run_tc_raw(L, s, G, a, d_err);
+        return prec == SV_PREC_TF32 ? run_tc_raw<TF32>(L, s, G, a, d_err) : run_tc_raw<BF16>(L, s, G, a, d_err);
     }
     const std::vector<unsigned char> img = build_a_image(mat, prec);
     cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);

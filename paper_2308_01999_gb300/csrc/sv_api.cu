@@ -213,18 +213,18 @@ sv_status_t sync_results(sv_ctx *h, int count) {
     return cuda_status(cudaStreamSynchronize(h->stream));
 }
 
-// Tensor-core blocks whose lowest target is below `low` take a slower kernel
-// variant: for TF32 below qubit 2 (measured on GB300 at 32 qubits: 10.5 ms per
-// block from lowest target 4 up, 11.9 ms at 3, 14.7 ms at 2, 16-16.4 ms at 0-1),
-// for split BF16 below qubit 4 (12.3-12.8 ms against 15-19 ms).
-int slow_below(sv_precision_t prec) { return prec == SV_PREC_TF32 ? 2 : 4; }
+// Tensor-core blocks whose lowest target is below qubit 2 take the slower
+// register-staged kernel (measured on GB300 at 32 qubits: 10.4-10.5 ms TF32 /
+// 11.2 ms split BF16 per block from lowest target 4 up, 11.9 / 12.5 ms at 3,
+// 14.7 / 15.4 ms at 2, 16-18 ms at 0-1).
+int slow_below(sv_precision_t) { return 2; }
 
 // Qubit relabelling for a fused run (Sec. II-C, qubit reordering, applied on one
 // GPU): qubits 0..low-1 are swapped with the `low` qubits that the fewest wide
 // blocks use (moving only some of them rarely helps, a block then keeps another
 // low target). Returns the pairs -- empty when the blocks it speeds up do not pay
 // for the two extra passes -- and the map logical -> physical. Cost model from
-// the measurements above: a slow block costs about 0.3-0.5 of a fast block more,
+// the measurements above: a slow block costs about 0.4-0.6 of a fast block more,
 // the two swap passes (one permutation pass each way over the whole state) about
 // 2 fast blocks, so at least 6 fewer slow blocks are needed.
 void choose_layout(const std::vector<svf::Item> &items, int n, int low, std::vector<int> &pairs,

@@ -9,8 +9,9 @@ c = 3 * 2^-18 + 384 * 2^-24 (split BF16); for a unitary gate that sum is at
 most sqrt(128) times the group's norm, so one gate changes the relative L2
 error by at most sqrt(128) * c and G gates by G times that. The tests assert
 these worst-case bounds and print the measured errors. The TF32 kernel for
-lowest targets >= 2 contracts over the 64 members in two FP32 sums of 64 terms
-(real and imaginary parts of G) joined by one addition, inside the same bound.
+lowest targets >= 2 (both precisions) contracts over the 64 members in two FP32
+sums of 64 terms (real and imaginary parts of G; split BF16: three products per
+term) joined by one addition, inside the same bounds.
 """
 import math
 
@@ -111,9 +112,9 @@ def test_native_and_tensor_core_agree_on_structure(env):
 
 @pytest.mark.parametrize("name", ["tf32", "bf16"])
 def test_low_targets_relabelled_by_index_bit_swaps(env, name):
-    """Wide blocks whose lowest target is below qubit 2 (TF32) or 4 (split
-    BF16) run after a qubit relabelling (two extra index-bit-swap passes) when
-    enough of them gain from it; the result is unchanged."""
+    """Wide blocks whose lowest target is below qubit 2 run after a qubit
+    relabelling (two extra index-bit-swap passes) when enough of them gain from
+    it; the result is unchanged."""
     torch, sv = env
     n = 24
     rng = gen.rng_for(91)
