@@ -496,7 +496,6 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_zall(const typename CT<R>::T *__restrict__ sv, int n, int m, int mt, double *__restrict__ partials) {
     using C = typename CT<R>::T;
-    __shared__ double red[kThreads / 32];
     __shared__ double row[kZMax + 1];
     const int mj = m - mt;
     const int t = threadIdx.x;
@@ -522,8 +521,8 @@ k_zall(const typename CT<R>::T *__restrict__ sv, int n, int m, int mt, double *_
         } else {
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const C a = sv[8 * c + e];
-                p[e] = a.x * a.x + a.y * a.y;
+                const C x = sv[8 * c + e];
+                p[e] = x.x * x.x + x.y * x.y;
             }
         }
         const R tot = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
@@ -549,33 +548,37 @@ k_zall(const typename CT<R>::T *__restrict__ sv, int n, int m, int mt, double *_
     for (int q = 0; q < 3; ++q) dB[q] += (double)fB[q];
 #pragma unroll
     for (int q = 0; q < kZJ; ++q) dJ[q] += (double)fJ[q];
-    // block sums in a fixed order: warp shuffles, then warps in order
-    auto bsum = [&](double v) {
+    // block sums in a fixed order, all values at once: value v = 0 total, 1..3 the
+    // chunk bits, 4 .. 4+mt-1 the thread-index bits, then the loop-counter bits;
+    // each warp reduces every value with shuffles, then thread v adds the warps'
+    // results in warp order
+    constexpr int kV = 4 + 8 + kZJ;
+    __shared__ double wred[kThreads / 32][kV];
+    const int nv = 4 + mt + mj;
+    auto warp_put = [&](double x, int v) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        __syncthreads();
-        if ((t & 31) == 0) red[t >> 5] = v;
-        __syncthreads();
-        double a = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) a += red[w];
-        return a;
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((t & 31) == 0) wred[t >> 5][v] = x;
     };
-    const double total = bsum(dT);
-    for (int q = 0; q < 3; ++q) {
-        const double v = bsum(dB[q]);
-        if (t == 0) row[q] = v;
-    }
-    for (int b = 0; b < mt; ++b) {
-        const double v = bsum(((t >> b) & 1) ? dT : 0.0);
-        if (t == 0) row[3 + b] = v;
-    }
+    warp_put(dT, 0);
 #pragma unroll
-    for (int q = 0; q < kZJ; ++q) {
-        if (q < mj) {                       // mj is the same for every thread
-            const double v = bsum(dJ[q]);
-            if (t == 0) row[3 + mt + q] = v;
-        }
+    for (int q = 0; q < 3; ++q) warp_put(dB[q], 1 + q);
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+        if (b < mt) warp_put(((t >> b) & 1) ? dT : 0.0, 4 + b);
+#pragma unroll
+    for (int q = 0; q < kZJ; ++q)
+        if (q < mj) warp_put(dJ[q], 4 + mt + q);
+    __syncthreads();
+    __shared__ double total_s;
+    if (t < nv) {
+        double acc = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) acc += wred[w][t];
+        if (t == 0) total_s = acc;
+        else row[t - 1] = acc;                 // qubit t - 1: chunk, thread and loop bits in order
     }
+    __syncthreads();
+    const double total = total_s;
     if (t == 0) {
         const uint64_t base = c0 << 3;
         for (int q = 3 + m; q < n; ++q) row[q] = ((base >> q) & 1u) ? total : 0.0;
@@ -603,7 +606,9 @@ __global__ void __launch_bounds__(64) k_zall_finish(const double *__restrict__ p
 template <typename R>
 cudaError_t zall_t(const LaunchCtx &L, const void *sv, int n, double *d_partials, int maxb, double *d_out) {
     using C = typename CT<R>::T;
-    // m = log2(chunks per block): about 512 blocks, at least 2^min(n-3, 8) chunks each, at most kZJ loop bits
+    // m = log2(chunks per block): about 512 blocks (measured faster than 2048 at 28
+    // qubits, where the single-block finish pass grows with the block count), at
+    // least 2^min(n-3, 8) chunks each, at most kZJ loop bits
     int m = n - 3 - 9;
     const int lo = (n - 3) < 8 ? (n - 3) : 8;
     if (m < lo) m = lo;
