@@ -137,3 +137,31 @@ def test_low_targets_relabelled_by_index_bit_swaps(env, name):
     err = rel_l2(got, ref)
     print(f"[tc] {name} low targets relabelled n={n}: {nf} blocks, rel L2 {err:.3e}")
     assert err <= nf * PER_GATE[name]
+
+
+@pytest.mark.parametrize("name", ["tf32", "bf16"])
+def test_full_size_32q_fused_echo(env, name):
+    """The 32-qubit brick wall (1900 gates, 32 GiB state) fused on the tensor
+    cores, then its inverse fused the same way, returns |0...0>: amplitude 0
+    comes back to 1 and the norm stays 1 within the per-block bound above --
+    a check at the full size, where no complex128 oracle fits on the host."""
+    torch, sv = env
+    n = 32
+    gates = gen.circuit_config2()
+    inverse = [gen.Gate(g.targets, g.matrix.conj().T, g.controls, g.control_values) for g in reversed(gates)]
+    psi = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    s = sv.StateVector(psi)
+    s.set_basis_state(0)
+    nf = s.apply_fused(gates, 6, prec_code(sv, name))
+    nb = s.apply_fused(inverse, 6, prec_code(sv, name))
+    s.check()
+    a0 = complex(psi[0].item())
+    norm = s.norm2()
+    bound = (nf + nb) * PER_GATE[name]
+    print(f"[tc] {name} 32q echo: {nf} + {nb} blocks, |a0 - 1| {abs(a0 - 1):.3e}, |norm - 1| {abs(norm - 1):.3e}, "
+          f"bound {bound:.3e}")
+    assert abs(a0 - 1) <= bound
+    assert abs(norm - 1) <= 2 * bound
+    s.close()
+    del psi
+    torch.cuda.empty_cache()
