@@ -131,9 +131,14 @@ SV_API sv_status_t sv_apply_matrix(sv_handle_t h, const int *targets, int n_targ
  * disjoint qubits, into blocks of at most max_fused_qubits qubits (1..6); each
  * block's matrix is composed on the host in FP64 and applied once. Blocks of
  * 5-6 qubits run in `prec` (tensor cores for TF32 / SPLIT_BF16), smaller ones
- * in native precision. *n_fused_out (may be NULL) receives the block count.
- * Asynchronous. Errors: as sv_apply_matrix for each gate; NOT_SUPPORTED for a
- * tensor-core precision on a complex128 state. */
+ * in native precision. With a tensor-core precision, when at least 6 wide
+ * blocks would have a target on qubit 0 or 1 (the slower tensor-core variant),
+ * the call first relabels qubits (Sec. II-C, qubit reordering: one index-bit
+ * swap pass moving the qubits that the fewest wide blocks use down to bits 0-1),
+ * applies the blocks in the new labels and swaps back; the result is the same.
+ * *n_fused_out (may be NULL) receives the block count. Asynchronous. Errors:
+ * as sv_apply_matrix for each gate; NOT_SUPPORTED for a tensor-core precision
+ * on a complex128 state. */
 SV_API sv_status_t sv_apply_fused(sv_handle_t h, const sv_gate_t *gates, int n_gates,
                            int max_fused_qubits, sv_precision_t prec, int *n_fused_out);
 
