@@ -561,7 +561,7 @@ constexpr int kEpiWarps3 = 8;                 // warps 6-13
 constexpr int kMmaWarp3 = kProdWarps3 + kEpiWarps3;
 constexpr int kThreads3 = (kMmaWarp3 + 1) * 32;
 constexpr int kTmemCols3 = 2 * 2 * kNT3;      // two accumulators of 256 columns
-constexpr int kRawMinLowTarget = 2;          // lowest target the launcher sends here
+constexpr int kRawMinLowTarget = 1;          // lowest target the launcher sends here
 
 struct TcCtl3 {
     unsigned long long landed[kStages3], full[kStages3], empty[kStages3], acc_full[2], acc_empty[2], done;
@@ -633,9 +633,15 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
-template <int P>
+// IL (lowest target t0 = 1..3): the amplitude pairs of member l run for
+// g = 2^(t0-1) pairs and are followed by those of member l ^ 1 (member bit 0 is
+// amplitude bit t0), so groups of g lanes alternate between l and l ^ 1 and every
+// copy and store instruction covers one contiguous run; otherwise (t0 >= 4, runs
+// of at least 128 bytes) all lanes of an instruction take one member and
+// consecutive pairs. lg = log2 g.
+template <int P, bool IL>
 __global__ void __launch_bounds__(kThreads3, 1)
-k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *__restrict__ d_err) {
+k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *__restrict__ d_err, int lg) {
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     if (smem_u32(smem_dyn) & 1023u) {
         if (threadIdx.x == 0) atomicExch(d_err, kErrSmemAlign);
@@ -676,23 +682,41 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
     const uint64_t ntl = G.n_tiles;
 
     if (warp < kCopyWarps3) {
-        // ---------------- copy: thread c takes amplitude pair c of all 64 members ----------------
-        // (a warp load is 32 consecutive pairs of one member: 512 contiguous bytes once
-        // the lowest target is 6 or more). The copies signal `landed` themselves
-        // (cp.async.mbarrier.arrive), so these threads never wait for data.
-        const int c = threadIdx.x;
-        const uint64_t pc = col_base((uint64_t)(2 * c), G);
-        const bool okc = (uint64_t)(2 * c) < G.n_cols;
+        // ---------------- copy ----------------
+        // Thread c takes amplitude pair c of all 64 members (a warp load is 32 consecutive
+        // pairs of one member: 512 contiguous bytes once the lowest target is 6 or more);
+        // with IL, thread t takes pairs c' and c' + 32 (c' = t % g + (t / 2g) g) of the
+        // members with bit 0 = (t / g) % 2.
+        // The copies signal `landed` themselves (cp.async.mbarrier.arrive), so these
+        // threads never wait for data.
+        const int tid = threadIdx.x;
+        const int g = 1 << lg;
+        const int c0 = IL ? (tid & (g - 1)) + ((tid >> (lg + 1)) << lg) : tid;
+        const uint64_t pc0 = col_base((uint64_t)(2 * c0), G);
+        const uint64_t pc1 = col_base((uint64_t)(2 * (c0 + 32)), G);
+        const bool ok0 = (uint64_t)(2 * c0) < G.n_cols, ok1 = (uint64_t)(2 * (c0 + 32)) < G.n_cols;
+        const int mb = IL ? (tid >> lg) & 1 : 0;
+        const uint64_t offb = IL ? G.off[mb] : 0;
         int i = 0;
         for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
             const int s = i % kStages3, u = i / kStages3;
             if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
-            const uint64_t tb = col_base(t * kNT3, G) | pc;
+            const uint64_t tb = col_base(t * kNT3, G);
             const uint32_t sb = sB0 + (uint32_t)(s * kB3);
+            if constexpr (IL) {
+                const uint64_t b0 = tb | pc0 | offb, b1 = tb | pc1 | offb;
+#pragma unroll 8
+                for (int m = 0; m < 32; ++m) {
+                    const int l = 2 * m + mb;
+                    const uint64_t om = G.off[2 * m];
+                    cp_async16(sb + mn_chunk(l, c0), ok0 ? sv + (b0 | om) : sv, ok0 ? 16u : 0u);
+                    cp_async16(sb + mn_chunk(l, c0 + 32), ok1 ? sv + (b1 | om) : sv, ok1 ? 16u : 0u);
+                }
+            } else {
+                const uint64_t b0 = tb | pc0;
 #pragma unroll 16
-            for (int l = 0; l < 64; ++l) {
-                const float2 *src = okc ? sv + (tb | G.off[l]) : sv;
-                cp_async16(sb + mn_chunk(l, c), src, okc ? 16u : 0u);
+                for (int l = 0; l < 64; ++l)
+                    cp_async16(sb + mn_chunk(l, c0), ok0 ? sv + (b0 | G.off[l]) : sv, ok0 ? 16u : 0u);
             }
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.landed[s]))
                          : "memory");
@@ -792,6 +816,10 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
         const int cst = 32 * hh + lane;                        // amplitude pair this lane stores
         const uint64_t pst = col_base((uint64_t)(2 * cst), G);
         const bool okst = (uint64_t)(2 * cst) < G.n_cols;
+        // IL: member bit 0 and pair offset of this lane, pairs 32 hh + pl and 32 hh + 16 + pl
+        const int lb = (lane >> lg) & 1, pl = (lane & ((1 << lg) - 1)) + ((lane >> (lg + 1)) << lg);
+        const uint64_t pst0 = IL ? col_base((uint64_t)(2 * (32 * hh + pl)), G) : 0;
+        const uint64_t pst1 = IL ? col_base((uint64_t)(2 * (32 * hh + 16 + pl)), G) : 0;
         int i = 0;
         for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
             const int s = i % kStages3, a = i & 1;
@@ -831,17 +859,24 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
             mbar_arrive(smem_u32(&S.acc_empty[a]));
             __syncwarp();
             // store: one member row per instruction, lanes on consecutive amplitude pairs
-            // (runs of 512 bytes when the lowest target is 6 or more). A store that
-            // scatters over 16 rows runs far below HBM bandwidth once the rows are MiB
-            // apart; these never do.
+            // (runs of 512 bytes when the lowest target is 6 or more; with IL, members
+            // l, l ^ 1 on alternate lane groups and 16 pairs). A store that scatters over
+            // 16 rows runs far below HBM bandwidth once the rows are MiB apart; these
+            // never do.
 #pragma unroll 4
             for (int r = 0; r < 16; ++r) {
-                const int l = 16 * q + r;
+                const int l = IL ? 16 * q + 2 * (r >> 1) + lb : 16 * q + r;
+                const int c = IL ? 32 * hh + 16 * (r & 1) + pl : cst;
                 float4 o;
                 asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
                              : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
-                             : "r"(sb + mn_chunk(l, cst)));
-                if (okst) *reinterpret_cast<float4 *>(sv + (tb | pst | G.off[l])) = o;
+                             : "r"(sb + mn_chunk(l, c)));
+                if constexpr (IL) {
+                    if ((uint64_t)(2 * c) < G.n_cols)
+                        *reinterpret_cast<float4 *>(sv + (tb | (r & 1 ? pst1 : pst0) | G.off[l])) = o;
+                } else {
+                    if (okst) *reinterpret_cast<float4 *>(sv + (tb | pst | G.off[l])) = o;
+                }
             }
             mbar_arrive(smem_u32(&S.empty[s]));
         }
@@ -949,13 +984,13 @@ std::vector<unsigned char> build_a_image3(const double *g, sv_precision_t prec) 
     return img;
 }
 
-template <int P>
-cudaError_t run_tc_raw(const LaunchCtx &L, float2 *sv, const TcGeom &G, const uint4 *d_a, int *d_err) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc6_raw<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+template <int P, bool IL>
+cudaError_t run_tc_raw(const LaunchCtx &L, float2 *sv, const TcGeom &G, const uint4 *d_a, int *d_err, int lg) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc6_raw<P, IL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
     if (e != cudaSuccess) return e;
     uint64_t grid = (uint64_t)L.num_sms;
     if (grid > G.n_tiles) grid = G.n_tiles;
-    k_tc6_raw<P><<<(unsigned)grid, kThreads3, kSmem3, L.stream>>>(sv, G, d_a, d_err);
+    k_tc6_raw<P, IL><<<(unsigned)grid, kThreads3, kSmem3, L.stream>>>(sv, G, d_a, d_err, lg);
     ++*L.launches;
     return cudaGetLastError();
 }
@@ -1006,7 +1041,13 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
         const std::vector<unsigned char> img = build_a_image3(mat, prec);
         cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
         if (e != cudaSuccess) return e;
-        return prec == SV_PREC_TF32 ? run_tc_raw<TF32>(L, s, G, a, d_err) : run_tc_raw<BF16>(L, s, G, a, d_err);
+        if (tpos[0] <= 3) {
+            const int lg = tpos[0] - 1;
+            return prec == SV_PREC_TF32 ? run_tc_raw<TF32, true>(L, s, G, a, d_err, lg)
+                                        : run_tc_raw<BF16, true>(L, s, G, a, d_err, lg);
+        }
+        return prec == SV_PREC_TF32 ? run_tc_raw<TF32, false>(L, s, G, a, d_err, 0)
+                                    : run_tc_raw<BF16, false>(L, s, G, a, d_err, 0);
     }
     const std::vector<unsigned char> img = build_a_image(mat, prec);
     cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
