@@ -570,6 +570,7 @@ struct TcCtl3 {
 };
 constexpr int kGuard3 = 2048;              // unused bytes after the last stage
 constexpr int kSmem3 = kA3 + kStages3 * kB3 + kGuard3 + (int)sizeof(TcCtl3);
+static_assert(kSmem3 <= 227 * 1024, "dynamic shared memory of the raw-operand kernel exceeds the per-block limit");
 
 // byte offset of the 16-byte chunk holding floats 4c .. 4c+3 of member row l
 // (c = amplitude pair, 0..63) in a stage: atom (c / 8, l / 8); inside it rows of
@@ -1032,11 +1033,10 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     G.n_tiles = (G.n_cols + kNT - 1) / kNT;
     float2 *s = reinterpret_cast<float2 *>(sv);
     const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
-    // Lowest target 2 or above (runs of at least 32 bytes): the raw-operand kernel,
-    // measured on GB300 (TF32) at one time per block whatever the other targets
-    // (10.5 ms for a 32-qubit state when the lowest target is 4 or more, 11.9 ms at
-    // 3, 14.7 ms at 2). With the lowest target at 1 its 16-byte runs make it slower
-    // (18.5 ms) than the register-staged kernel below (16.4).
+    // Lowest target 1 or above (qubit 0 free): the raw-operand kernel, measured on
+    // GB300 (TF32, 32-qubit state) at 10.4-10.5 ms per block for lowest target 3 or
+    // more whatever the other targets, 12.7 ms at 2, 14.8 ms at 1; with qubit 0 a
+    // target the register-staged kernel below (about 16 ms).
     if (tpos[0] >= kRawMinLowTarget && n >= 8) {
         const std::vector<unsigned char> img = build_a_image3(mat, prec);
         cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);

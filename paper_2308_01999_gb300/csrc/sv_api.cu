@@ -213,10 +213,10 @@ sv_status_t sync_results(sv_ctx *h, int count) {
     return cuda_status(cudaStreamSynchronize(h->stream));
 }
 
-// Tensor-core blocks whose lowest target is below qubit 2 take the slower
-// register-staged kernel (measured on GB300 at 32 qubits: 10.4-10.5 ms TF32 /
-// 11.2 ms split BF16 per block from lowest target 4 up, 11.9 / 12.5 ms at 3,
-// 14.7 / 15.4 ms at 2, 16-18 ms at 0-1).
+// Tensor-core blocks whose lowest target is below qubit 2 are the slow ones
+// (measured on GB300 at 32 qubits, TF32 / split BF16: 10.4 / 11.2 ms per block for
+// lowest target 3 or more, 12.7 / 13.6 ms at 2, 14.8 / 15.4 ms at 1 and about
+// 16 ms at 0, where the register-staged kernel runs).
 int slow_below(sv_precision_t) { return 2; }
 
 // Qubit relabelling for a fused run (Sec. II-C, qubit reordering, applied on one
