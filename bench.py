@@ -258,16 +258,17 @@ def run_ours(args):
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_gates)]
           for _ in range(args.steps)]
 
-    def one_step(step_events=None):
+    def one_step(step_events=None, st=None):
+        st = st or s
         for i, g in enumerate(gates):
             if step_events is not None:
                 step_events[i][0].record(stream)
-            s.apply_gate(g)
+            st.apply_gate(g)
             if step_events is not None:
                 step_events[i][1].record(stream)
-        z = s.expectation_z_all()
-        e = s.expectation_pauli(paulis, sites)
-        p = s.measure_probs([0, N_QUBITS - 1])
+        z = st.expectation_z_all()
+        e = st.expectation_pauli(paulis, sites)
+        p = st.measure_probs([0, N_QUBITS - 1])
         return z, e, p
 
     with torch.cuda.stream(stream):
@@ -295,23 +296,37 @@ def run_ours(args):
         ms = t0.elapsed_time(t1) / args.steps
         launches = (s.launches() - launches0) // max(1, args.steps) * args.steps
 
-        # end to end through the C ABI with host buffers: pinned initial state in,
-        # final state out, every step
+        # end to end through the C ABI with host buffers: every step copies a full
+        # initial state in from pinned host memory, runs the circuit and the
+        # reductions, and copies the final state out. Two device states alternate
+        # on two streams, so that step k+1's input copy and step k's output copy
+        # (sv_copy_*_async) run while the other state computes.
         h_in = torch.zeros(1 << N_QUBITS, dtype=torch.complex64, pin_memory=True)
         h_in[0] = 1
-        h_out = torch.empty(1 << N_QUBITS, dtype=torch.complex64, pin_memory=True)
+        h_out = [torch.empty(1 << N_QUBITS, dtype=torch.complex64, pin_memory=True) for _ in range(2)]
+        stream2 = torch.cuda.Stream(dev)
+        psi2 = torch.empty_like(psi)
+        s2 = sv.StateVector(psi2, stream2)
+        pair = [s, s2]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e_steps = max(1, min(args.steps, 2))
+        e_steps = max(2, min(args.steps, 4))
         torch.cuda.synchronize()
         barrier()
         e0.record(stream)
-        for _ in range(e_steps):
-            sv.sv_copy_from_host(s.handle, h_in.data_ptr())
-            one_step()
-            sv.sv_copy_to_host(s.handle, h_out.data_ptr())
+        stream2.wait_event(e0)
+        sv.sv_copy_from_host_async(pair[0].handle, h_in.data_ptr())
+        for k in range(e_steps):
+            cur, nxt = pair[k % 2], pair[(k + 1) % 2]
+            if k + 1 < e_steps:
+                sv.sv_copy_from_host_async(nxt.handle, h_in.data_ptr())
+            one_step(st=cur)
+            sv.sv_copy_to_host_async(cur.handle, h_out[k % 2].data_ptr())
+        stream.wait_stream(stream2)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
+        s2.close()
+        del psi2
         e2e_ms = e0.elapsed_time(e1) / e_steps
 
     ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev)
@@ -362,7 +377,9 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "e2e": {"value": round(job_throughput(nbytes, world, e2e_ms), 1), "unit": UNIT,
                 "h2d_bytes_per_step": AMP_BYTES << N_QUBITS, "d2h_bytes_per_step": AMP_BYTES << N_QUBITS,
-                "ms_per_step": round(e2e_ms, 3)},
+                "ms_per_step": round(e2e_ms, 3),
+                "copies": "full state in and out each step; two device states alternate so the copies "
+                          "overlap the other state's gates"},
         "clocks": clk,
         "cpu_baseline": cpu,
     }

@@ -111,6 +111,15 @@ SV_API sv_status_t sv_set_basis_state(sv_handle_t h, uint64_t index);
 SV_API sv_status_t sv_copy_from_host(sv_handle_t h, const void *host);
 SV_API sv_status_t sv_copy_to_host(sv_handle_t h, void *host);
 
+/* The same copies, only enqueued on the handle's stream (they return at once).
+ * The host buffer must stay valid, and must not be reused, until the stream
+ * has passed the copy; with pinned host memory the copy overlaps work on other
+ * streams (e.g. a second state's gates), with pageable memory the CUDA runtime
+ * stages it and the call may block. Errors: INVALID_ARGUMENT for NULL
+ * pointers, CUDA. */
+SV_API sv_status_t sv_copy_from_host_async(sv_handle_t h, const void *host);
+SV_API sv_status_t sv_copy_to_host_async(sv_handle_t h, void *host);
+
 /* Gate application (Table I; Sec. II-B): psi <- G psi with G the 2^k x 2^k
  * matrix on targets (k = n_targets, 1..6), applied where the controls hold.
  * adjoint != 0 applies the conjugate transpose. The library inspects the

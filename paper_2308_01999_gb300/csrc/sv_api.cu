@@ -386,6 +386,20 @@ sv_status_t sv_copy_to_host(sv_handle_t h, void *host) {
     return cuda_status(cudaStreamSynchronize(h->stream));
 }
 
+sv_status_t sv_copy_from_host_async(sv_handle_t h, const void *host) {
+    if (!h || !host) return SV_ERR_INVALID_ARGUMENT;
+    DeviceGuard dg(h->device);
+    const size_t bytes = (size_t(1) << h->n) * (h->dt == SV_C64 ? 8 : 16);
+    return cuda_status(cudaMemcpyAsync(h->sv, host, bytes, cudaMemcpyHostToDevice, h->stream));
+}
+
+sv_status_t sv_copy_to_host_async(sv_handle_t h, void *host) {
+    if (!h || !host) return SV_ERR_INVALID_ARGUMENT;
+    DeviceGuard dg(h->device);
+    const size_t bytes = (size_t(1) << h->n) * (h->dt == SV_C64 ? 8 : 16);
+    return cuda_status(cudaMemcpyAsync(host, h->sv, bytes, cudaMemcpyDeviceToHost, h->stream));
+}
+
 sv_status_t sv_apply_matrix(sv_handle_t h, const int *targets, int n_targets, const int *controls,
                             const int *control_values, int n_controls, const double *matrix, int adjoint) {
     sv_status_t s = check_gate_args(h, targets, n_targets, controls, control_values, n_controls, matrix);

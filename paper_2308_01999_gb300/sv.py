@@ -18,7 +18,8 @@ import numpy as np
 
 __all__ = [
     "SvError", "lib", "sv_create", "sv_destroy", "sv_set_stream", "sv_set_state_pointer",
-    "sv_set_basis_state", "sv_copy_from_host", "sv_copy_to_host", "sv_apply_matrix",
+    "sv_set_basis_state", "sv_copy_from_host", "sv_copy_to_host", "sv_copy_from_host_async",
+    "sv_copy_to_host_async", "sv_apply_matrix",
     "sv_apply_fused", "sv_fuse_plan", "sv_expectation_pauli", "sv_measure_probs", "sv_collapse",
     "sv_measure", "sv_norm2", "sv_check_device_status", "sv_launch_count", "sv_status_string",
     "SV_C64", "SV_C128", "SV_PREC_NATIVE", "SV_PREC_TF32", "SV_PREC_SPLIT_BF16", "StateVector",
@@ -41,7 +42,8 @@ EXPORTED = [
     "sv_check_device_status", "sv_launch_count", "sv_status_string", "sv_expectation_pauli_noalloc",
     "sv_batch_create", "sv_batch_destroy", "sv_batch_compile", "sv_batch_info", "sv_batch_launch",
     "sv_batch_results", "sv_swap_index_bits", "sv_apply_pauli_rotation", "sv_sample",
-    "sv_check_bounded_wait", "sv_apply_fused_ex", "sv_fuse_plan_ex",
+    "sv_check_bounded_wait", "sv_apply_fused_ex", "sv_fuse_plan_ex", "sv_copy_from_host_async",
+    "sv_copy_to_host_async",
 ]
 
 
@@ -78,6 +80,7 @@ def lib():
             "sv_destroy": [_VP], "sv_set_stream": [_VP, _VP], "sv_set_state_pointer": [_VP, _VP],
             "sv_set_basis_state": [_VP, C.c_uint64],
             "sv_copy_from_host": [_VP, _VP], "sv_copy_to_host": [_VP, _VP],
+            "sv_copy_from_host_async": [_VP, _VP], "sv_copy_to_host_async": [_VP, _VP],
             "sv_apply_matrix": [_VP, _I, C.c_int, _I, _I, C.c_int, _D, C.c_int],
             "sv_apply_fused": [_VP, C.POINTER(sv_gate_t), C.c_int, C.c_int, C.c_int, _I],
             "sv_fuse_plan": [C.POINTER(sv_gate_t), C.c_int, C.c_int, C.c_int, C.c_int, _I, _I, _I, _D],
@@ -161,6 +164,14 @@ def sv_copy_from_host(h: int, host_ptr: int):
 
 def sv_copy_to_host(h: int, host_ptr: int):
     _check(lib().sv_copy_to_host(_VP(h), _VP(host_ptr)), "sv_copy_to_host")
+
+
+def sv_copy_from_host_async(h: int, host_ptr: int):
+    _check(lib().sv_copy_from_host_async(_VP(h), _VP(host_ptr)), "sv_copy_from_host_async")
+
+
+def sv_copy_to_host_async(h: int, host_ptr: int):
+    _check(lib().sv_copy_to_host_async(_VP(h), _VP(host_ptr)), "sv_copy_to_host_async")
 
 
 def sv_apply_matrix(h: int, targets, matrix, controls=(), control_values=None, adjoint: bool = False):
