@@ -3,18 +3,24 @@
 // memory-bound gates into one 2^k x 2^k product; beyond k = 5 (complex64) the
 // product is compute-bound on CUDA cores, so here it runs on the tensor cores.
 //
-// The product. View the state as 64 x 2^(n-6): column c holds the 64 members
-// of group c (the amplitudes whose non-target bits spell c). With x_c the 128
-// reals (re, im interleaved: K index 2j + e for member j) of column c,
-//   out_c = A x_c,  A[2j+e][2l+f] = the real 2x2 block [[Re, -Im], [Im, Re]] of G[j][l],
-// so one fused gate is the real GEMM  D(128 x N) = A(128 x 128) * B(128 x N)
-// with B's columns the state columns. A is the same for every column.
+// View the state as 64 x 2^(n-6): column c holds the 64 members of group c (the
+// amplitudes whose non-target bits spell c); one fused gate G is the same
+// product for every column. Two kernels:
+//   k_tc6_raw (qubit 0 not a target, the common case): the state tile itself is
+//     the MN-major B operand and the contraction runs over the 64 members
+//     (described at the kernel);
+//   k_tc6 (qubit 0 a target): with x_c the 128 reals of column c (re, im
+//     interleaved: K index 2j + e for member j),
+//       out_c = A x_c,  A[2j+e][2l+f] = the real 2x2 block [[Re, -Im], [Im, Re]] of G[j][l],
+//     i.e. the real GEMM D(128 x N) = A(128 x 128) * B(128 x N) with B's
+//     columns the state columns, staged through registers into the K-major
+//     128-byte-swizzled layout.
 //
 // Precision: TF32 (operands rounded to nearest TF32, FP32 accumulation) or
 // split BF16 (x = hi + lo with hi, lo BF16; A*B ~ Ahi*Bhi + Ahi*Blo + Alo*Bhi,
 // three MMAs into one FP32 accumulator).
 //
-// Kernel structure (one persistent CTA per SM, 544 threads):
+// k_tc6 structure (one persistent CTA per SM, 544 threads):
 //   warps 0-7   producers: read a tile of 128 columns x 64 members from HBM in
 //               address order (16-byte loads, each warp load one contiguous
 //               512-byte run, whatever the target positions), round or split,
@@ -23,9 +29,10 @@
 //   warp 16     MMA issuer: one thread issues tcgen05.mma (M = N = 128) into one
 //               of two TMEM accumulators and commits to mbarriers;
 //   warps 8-15  epilogue: tcgen05.ld of the accumulator rows (warp w reads TMEM
-//               lanes 32*(w%4)..+31, columns of one half of the tile), pair up
-//               the (re, im) rows of each member with one shuffle, and store back
-//               in place (16-byte stores unless qubit 0 is a target).
+//               lanes 32*(w%4)..+31, columns of one half of the tile), stage
+//               them in shared memory and store runs of 16 members of one
+//               column (qubit 0 being a target, members 2m and 2m + 1 are
+//               adjacent amplitudes).
 // Addresses: a tile starts at a multiple of 128 columns, so the amplitude
 // offset of column t*128 + i is col_base(t*128) | pd[i], with the deposit table
 // pd[] computed once per CTA.
@@ -60,11 +67,8 @@ constexpr int kErrTimeout = 0x7c01;
 
 enum Prec { TF32 = 1, BF16 = 2 };
 
-// Control block in dynamic shared memory after the operand area, and (for the
-// address-order producer only) tile tables in static shared memory, so that
-// each instantiation asks for only what it uses. At 196 KB or less per CTA the
-// SM keeps 60 KB of L1, which the column producer's 64 KB of loads in flight
-// need; the staged epilogues (17 KB more) move the CTA to the 228 KB carve-out.
+// Control block in dynamic shared memory after the operand area and the
+// epilogue staging; the producer's tile tables in static shared memory.
 struct TcCtl {
     unsigned long long full[2], empty[2], acc_full[2], acc_empty[2], done;
     uint16_t pd[kNT];   // column offset i in a tile -> amplitude offset (the 7 lowest non-target
@@ -80,10 +84,10 @@ struct TcTab {
 };
 constexpr int kErrSmemAlign = 0x7c02;
 
-// dynamic shared memory of one instantiation: operands, staging, control
+// dynamic shared memory of k_tc6: operands, staging, control
 __host__ __device__ constexpr int tc_stage_off() { return kAImg + 2 * kBStage; }
-__host__ __device__ constexpr int tc_ctl_off(int epi_direct) { return tc_stage_off() + (epi_direct ? 0 : kEpiStage); }
-__host__ __device__ constexpr int tc_smem_bytes(int epi_direct) { return tc_ctl_off(epi_direct) + (int)sizeof(TcCtl); }
+__host__ __device__ constexpr int tc_ctl_off() { return tc_stage_off() + kEpiStage; }
+__host__ __device__ constexpr int tc_smem_bytes() { return tc_ctl_off() + (int)sizeof(TcCtl); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -235,12 +239,7 @@ __device__ __forceinline__ uint32_t sw128(int kb, int r, int chunk) {
     return (uint32_t)(kb * (kNT * 128) + (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4));
 }
 
-// PROD_COLS: producers load lane-per-column (lowest target >= 4), else in address order.
-// EPI: EPI_DIRECT stores 16-byte column pairs straight from the accumulator rows
-// (qubit 0 free, the rows a warp writes within a few MiB); EPI_COLS / EPI_MEMBERS
-// stage through shared memory and store runs of columns / of members.
-enum { EPI_DIRECT = 0, EPI_COLS = 1, EPI_MEMBERS = 2 };
-template <int P, bool PROD_COLS, int EPI>
+template <int P>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *__restrict__ d_err) {
     // The operand area starts the dynamic shared memory and must be 1024-byte
@@ -252,7 +251,7 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
         if (threadIdx.x == 0) atomicExch(d_err, kErrSmemAlign);
         return;
     }
-    TcCtl &S = *reinterpret_cast<TcCtl *>(smem_dyn + tc_ctl_off(EPI == EPI_DIRECT));
+    TcCtl &S = *reinterpret_cast<TcCtl *>(smem_dyn + tc_ctl_off());
     __shared__ TcTab T;
     unsigned char *sA = smem_dyn;
     unsigned char *sB0 = smem_dyn + kAImg;     // stage s at sB0 + s * kBStage
@@ -272,7 +271,7 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
     }
     // A tile starts at a multiple of kNT columns, so col_base(t*kNT + i) = col_base(t*kNT) | pd[i]
     if (threadIdx.x < kNT) S.pd[threadIdx.x] = (uint16_t)col_base((uint64_t)threadIdx.x, G);
-    if (!PROD_COLS && threadIdx.x >= kNT && threadIdx.x < kNT + 192) {
+    if (threadIdx.x >= kNT && threadIdx.x < kNT + 192) {
         // tile bit b (0..12) in ascending position: either target tj (member bit tj)
         // or the k-th lowest non-target (column bit k); positions >= n only occur
         // for states under 13 qubits and land in columns >= n_cols (never loaded)
@@ -313,51 +312,6 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
 
     if (warp < kProdWarps) {
         // ---------------- producers ----------------
-        if constexpr (PROD_COLS) {
-            // the lowest target is at least 4: lane n takes column n (8-byte loads, consecutive
-            // lanes on consecutive columns, 32 loads in flight per thread) and stores
-            // whole 16-byte chunks of the swizzled operand, free of bank conflicts
-            const int n = threadIdx.x & (kNT - 1);          // column within the tile
-            const int qhalf = threadIdx.x >> 7;             // member quads 8*qhalf .. 8*qhalf+7
-            int i = 0;
-            for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
-                const int s = i & 1, u = i >> 1;
-                if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
-                const uint64_t c = t * kNT + n;
-                const bool valid = c < G.n_cols;
-                const uint64_t cb = valid ? (col_base(t * kNT, G) | S.pd[n]) : 0;
-                float2 v[32];
-    #pragma unroll
-                for (int m = 0; m < 32; ++m) {
-                    const int j = qhalf * 32 + m;
-                    v[m] = valid ? sv[cb + G.off[j]] : make_float2(0.f, 0.f);
-                }
-                unsigned char *sb = sB0 + s * kBStage;
-    #pragma unroll
-                for (int qq = 0; qq < 8; ++qq) {
-                    const int q = qhalf * 8 + qq;     // members 4q .. 4q+3 = K 8q .. 8q+7
-                    const float2 a0 = v[4 * qq], a1 = v[4 * qq + 1], a2 = v[4 * qq + 2], a3 = v[4 * qq + 3];
-                    if constexpr (P == TF32) {
-                        const int kb = q >> 2, ch = 2 * (q & 3);
-                        uint4 w0 = make_uint4(to_tf32(a0.x), to_tf32(a0.y), to_tf32(a1.x), to_tf32(a1.y));
-                        uint4 w1 = make_uint4(to_tf32(a2.x), to_tf32(a2.y), to_tf32(a3.x), to_tf32(a3.y));
-                        *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch)) = w0;
-                        *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch + 1)) = w1;
-                    } else {
-                        const int kb = q >> 3, ch = q & 7;
-                        uint4 hi, lo;
-                        split_bf16(a0.x, a0.y, hi.x, lo.x);
-                        split_bf16(a1.x, a1.y, hi.y, lo.y);
-                        split_bf16(a2.x, a2.y, hi.z, lo.z);
-                        split_bf16(a3.x, a3.y, hi.w, lo.w);
-                        *reinterpret_cast<uint4 *>(sb + sw128(kb, n, ch)) = hi;
-                        *reinterpret_cast<uint4 *>(sb + kBStage / 2 + sw128(kb, n, ch)) = lo;
-                    }
-                }
-                fence_proxy_async();
-                mbar_arrive(smem_u32(&S.full[s]));
-            }
-        } else {
             // Each thread loads 16 pairs of adjacent amplitudes of the tile in address
             // order (lane-consecutive 16-byte loads: every warp load is one contiguous
             // 512-byte run), then scatters each amplitude to its (column, member) slot
@@ -403,7 +357,6 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
                 fence_proxy_async();
                 mbar_arrive(smem_u32(&S.full[s]));
             }
-        }
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
@@ -449,19 +402,15 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
         // Each warp reads 16 accumulator columns of its 32 TMEM lanes (16 members
         // x re/im) at a time, stages them in shared memory, and stores them back
         // so that every store instruction writes contiguous runs: 16 consecutive
-        // columns of one member row (qubit 0 free) or 16 consecutive members of
-        // one column (qubit 0 a target). Lane-per-row stores that scatter over 16
-        // rows run at a fraction of HBM bandwidth when the rows are far apart.
+        // members of one column (qubit 0 is a target, so members 2m and 2m + 1
+        // are adjacent amplitudes). Lane-per-row stores that scatter over 16 rows
+        // run at a fraction of HBM bandwidth when the rows are far apart.
         const int ew = warp - kProdWarps;
         const int sub = warp & 3;                   // TMEM lanes 32*sub .. 32*sub+31: members 16*sub .. +15
         const int half = ew >> 2;                   // columns 64*half .. 64*half+63 of the tile
         float *stg = reinterpret_cast<float *>(smem_dyn + tc_stage_off()) + ew * 32 * kStgPitch;
-        uint64_t offr[8];                           // member offsets this lane stores
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int jj = EPI == EPI_COLS ? 2 * r + (lane >> 4) : (lane & 15);
-            offr[r] = G.off[16 * sub + jj];
-        }
+        const int jj = lane & 15;                   // member 16*sub + jj
+        const uint64_t offj = G.off[16 * sub + jj];
         int i = 0;
         for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
             const int a = i & 1, u = i >> 1;
@@ -469,33 +418,6 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
             tc_fence_after();
             const uint64_t tb = col_base(t * kNT, G);
             const uint64_t tcol = t * kNT;
-            if constexpr (EPI == EPI_DIRECT) {
-                // row m = 2j + e of this lane: the even lane stores columns (c, c+1) of
-                // member j, the odd lane (c+2, c+3), after one exchange of halves
-                const int e = lane & 1;
-                const uint64_t tbj = tb + G.off[16 * sub + (lane >> 1)];
-#pragma unroll 1
-                for (int cc = 0; cc < 2; ++cc) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * kNT + half * 64 + cc * 32), v);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float s0 = e ? v[4 * q] : v[4 * q + 2];
-                        const float s1 = e ? v[4 * q + 1] : v[4 * q + 3];
-                        const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1);
-                        const float r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-                        const int ci = half * 64 + cc * 32 + 4 * q + (e ? 2 : 0);
-                        if (tcol + ci < G.n_cols) {
-                            const float4 o = e ? make_float4(r0, v[4 * q + 2], r1, v[4 * q + 3])
-                                               : make_float4(v[4 * q], r0, v[4 * q + 1], r1);
-                            *reinterpret_cast<float4 *>(sv + (tbj | S.pd[ci])) = o;
-                        }
-                    }
-                }
-                tc_fence_before();
-                mbar_arrive(smem_u32(&S.acc_empty[a]));
-                continue;
-            }
 #pragma unroll 1
             for (int cc = 0; cc < 4; ++cc) {
                 float v[16];
@@ -506,12 +428,11 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
                 const int c0 = half * 64 + cc * 16;
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    const int jj = EPI == EPI_COLS ? 2 * r + (lane >> 4) : (lane & 15);
-                    const int col = EPI == EPI_COLS ? (lane & 15) : 2 * r + (lane >> 4);
+                    const int col = 2 * r + (lane >> 4);
                     const float re = stg[(2 * jj) * kStgPitch + col];
                     const float im = stg[(2 * jj + 1) * kStgPitch + col];
                     const int ci = c0 + col;
-                    if (tcol + ci < G.n_cols) sv[(tb | S.pd[ci]) + offr[r]] = make_float2(re, im);
+                    if (tcol + ci < G.n_cols) sv[(tb | S.pd[ci]) + offj] = make_float2(re, im);
                 }
                 __syncwarp();
             }
@@ -833,24 +754,24 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 2 * kNT3 + hh * kNT3 + cc * 32), v);
                 // v[2u + f] = row product for amplitude 64 hh + 16 cc + u, component f. Of each
-                // four amplitudes 4P .. 4P+3 the Re lane finishes the first two, the Im lane
+                // four amplitudes 4g .. 4g+3 the Re lane finishes the first two, the Im lane
                 // the last two; each sends the partner the four products it needs.
 #pragma unroll
-                for (int P = 0; P < 4; ++P) {
+                for (int g = 0; g < 4; ++g) {
                     float r[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        r[k] = __shfl_xor_sync(0xffffffffu, e ? v[8 * P + k] : v[8 * P + 4 + k], 16);
+                        r[k] = __shfl_xor_sync(0xffffffffu, e ? v[8 * g + k] : v[8 * g + 4 + k], 16);
                     float4 o;
                     if (e == 0) {
-                        o = make_float4(v[8 * P] - r[1], v[8 * P + 1] + r[0], v[8 * P + 2] - r[3], v[8 * P + 3] + r[2]);
+                        o = make_float4(v[8 * g] - r[1], v[8 * g + 1] + r[0], v[8 * g + 2] - r[3], v[8 * g + 3] + r[2]);
                     } else {
-                        o = make_float4(r[0] - v[8 * P + 5], r[1] + v[8 * P + 4], r[2] - v[8 * P + 7],
-                                        r[3] + v[8 * P + 6]);
+                        o = make_float4(r[0] - v[8 * g + 5], r[1] + v[8 * g + 4], r[2] - v[8 * g + 7],
+                                        r[3] + v[8 * g + 6]);
                     }
                     // amplitude pair c of the tile, staged as one 16-byte chunk (conflict free:
                     // the 16 rows of an instruction fall in four 32-byte bank groups)
-                    const int c = 32 * hh + 8 * cc + 2 * P + e;
+                    const int c = 32 * hh + 8 * cc + 2 * g + e;
                     asm volatile("st.shared.v4.f32 [%0], {%1,%2,%3,%4};" ::"r"(sb + mn_chunk(j, c)), "f"(o.x),
                                  "f"(o.y), "f"(o.z), "f"(o.w)
                                  : "memory");
@@ -996,10 +917,10 @@ cudaError_t run_tc_raw(const LaunchCtx &L, float2 *sv, const TcGeom &G, const ui
     return cudaGetLastError();
 }
 
-template <int P, bool PROD_COLS, int EPI>
+template <int P>
 cudaError_t run_tc(const LaunchCtx &L, float2 *sv, const TcGeom &G, const uint4 *d_a, int *d_err) {
-    auto kern = k_tc6<P, PROD_COLS, EPI>;
-    const int smem = tc_smem_bytes(EPI == EPI_DIRECT);
+    auto kern = k_tc6<P>;
+    const int smem = tc_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     uint64_t grid = (uint64_t)L.num_sms;
@@ -1033,11 +954,12 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     G.n_tiles = (G.n_cols + kNT - 1) / kNT;
     float2 *s = reinterpret_cast<float2 *>(sv);
     const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
-    // Lowest target 1 or above (qubit 0 free): the raw-operand kernel, measured on
-    // GB300 (TF32, 32-qubit state) at 10.4-10.5 ms per block for lowest target 3 or
-    // more whatever the other targets, 12.7 ms at 2, 14.8 ms at 1; with qubit 0 a
-    // target the register-staged kernel below (about 16 ms).
-    if (tpos[0] >= kRawMinLowTarget && n >= 8) {
+    // Lowest target 1 or above (qubit 0 free; then n >= 7 and a tile holds whole
+    // amplitude pairs): the raw-operand kernel, measured on GB300 (TF32, 32-qubit
+    // state) at 10.4-10.5 ms per block for lowest target 3 or more whatever the
+    // other targets, 12.7 ms at 2, 14.8 ms at 1; with qubit 0 a target the
+    // register-staged kernel below (about 16 ms).
+    if (tpos[0] >= kRawMinLowTarget && n >= 7) {
         const std::vector<unsigned char> img = build_a_image3(mat, prec);
         cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
         if (e != cudaSuccess) return e;
@@ -1052,26 +974,8 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     const std::vector<unsigned char> img = build_a_image(mat, prec);
     cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
     if (e != cudaSuccess) return e;
-    // Loads: lowest target >= 4 means 16 consecutive columns are contiguous, so lanes
-    // take columns; below that, loads follow address order. Stores: with qubit 0 a
-    // target, runs of members; otherwise direct column pairs when the 16 rows a warp
-    // writes span less than 8 MiB (fourth target below 20), else staged column runs.
-    const int t0 = tpos[0];
-    const bool cols = t0 >= 4;
-    const int epi = t0 == 0 ? EPI_MEMBERS : (tpos[3] < 20 ? EPI_DIRECT : EPI_COLS);
-#define SV_TC_RUN(PR)                                                                           \
-    do {                                                                                        \
-        if (cols) {                                                                             \
-            if (epi == EPI_DIRECT) return run_tc<PR, true, EPI_DIRECT>(L, s, G, a, d_err);      \
-            return run_tc<PR, true, EPI_COLS>(L, s, G, a, d_err);                              \
-        }                                                                                       \
-        if (epi == EPI_DIRECT) return run_tc<PR, false, EPI_DIRECT>(L, s, G, a, d_err);         \
-        if (epi == EPI_COLS) return run_tc<PR, false, EPI_COLS>(L, s, G, a, d_err);             \
-        return run_tc<PR, false, EPI_MEMBERS>(L, s, G, a, d_err);                              \
-    } while (0)
-    if (prec == SV_PREC_TF32) SV_TC_RUN(TF32);
-    SV_TC_RUN(BF16);
-#undef SV_TC_RUN
+    // qubit 0 a target: the register-staged kernel
+    return prec == SV_PREC_TF32 ? run_tc<TF32>(L, s, G, a, d_err) : run_tc<BF16>(L, s, G, a, d_err);
 }
 
 cudaError_t launch_wait_probe(const LaunchCtx &L, int *d_err, long long cycles) {

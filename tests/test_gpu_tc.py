@@ -53,7 +53,9 @@ def rel_l2(got, ref):
                                        # several tiles, far and contiguous targets
                                        (9, (3, 4, 5, 6, 7, 8)), (11, (3, 5, 6, 8, 9, 10)),
                                        (16, (5, 9, 10, 12, 14, 15)), (20, (3, 8, 12, 16, 18, 19)),
-                                       (17, (11, 12, 13, 14, 15, 16))])
+                                       (17, (11, 12, 13, 14, 15, 16)),
+                                       # 7 qubits, qubit 0 free: a single pair of columns
+                                       (7, (1, 2, 3, 4, 5, 6))])
 def test_single_six_qubit_gate(env, name, n, targets):
     torch, sv = env
     rng = gen.rng_for(n * 100 + targets[0])
