@@ -540,9 +540,10 @@ def run_batch(args):
         tune = {}
         best = None
         buf = None
-        for w in (1, 2, 3, 4):
+        # fusion width x register-window width (the per-thread chunk of a pass)
+        for w, win in ((1, 4), (2, 4), (3, 4), (4, 4), (1, 3), (2, 3), (1, 0), (2, 0)):
             t0 = time.perf_counter()
-            info = b.compile(states, fusion_width=w)
+            info = b.compile(states, fusion_width=w, window_qubits=win)
             comp = time.perf_counter() - t0
             if buf is None:
                 buf = torch.empty(b.state_amps, dtype=torch.complex64, device=dev)
@@ -556,13 +557,14 @@ def run_batch(args):
             e1.record(stream)
             res = b.results()
             ms = e0.elapsed_time(e1) / reps
-            tune[w] = {"ms": round(ms, 3), "states_per_s": round(len(states) / (ms * 1e-3), 1),
-                       "ops": info["ops"], "stages": info["stages"], "compile_s": round(comp, 2)}
+            key = f"fusion{w}_window{win}"
+            tune[key] = {"ms": round(ms, 3), "states_per_s": round(len(states) / (ms * 1e-3), 1),
+                         "ops": info["ops"], "stages": info["stages"], "compile_s": round(comp, 2)}
             if best is None or ms < tune[best]["ms"]:
-                best = w
-            print(json.dumps({"width": w, **tune[w]}), file=sys.stderr, flush=True)
+                best = key
+            print(json.dumps({"config": key, **tune[key]}), file=sys.stderr, flush=True)
         out["autotune"] = tune
-        out["fusion_width"] = best
+        out["fusion_width"], out["window_qubits"] = (int(x) for x in best.replace("fusion", "").split("_window"))
         out["batched_states_per_s"] = tune[best]["states_per_s"]
         out["batched_ms"] = tune[best]["ms"]
         b.close()

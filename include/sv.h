@@ -320,6 +320,22 @@ SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, 
                                     const sv_gate_t *gates, int n_gates_total, const int *paulis,
                                     int fusion_width);
 
+/* Compile options. window_qubits bounds the register windows: runs of ops
+ * with at most 2 targets on at most that many local qubits applied to
+ * amplitudes held in registers, one shared-memory round trip per run (0 = no
+ * windows, else 2..4; tiles under 13 qubits use narrower windows so that every
+ * thread keeps a group). sv_batch_compile uses window_qubits = 4. */
+typedef struct {
+    int fusion_width;     /* 1..4 */
+    int window_qubits;    /* 0, 2, 3 or 4 */
+} sv_batch_options_t;
+
+/* sv_batch_compile with explicit options; errors as sv_batch_compile, and
+ * INVALID_ARGUMENT for options out of range or NULL. */
+SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *items, int n_items,
+                                       const sv_gate_t *gates, int n_gates_total, const int *paulis,
+                                       const sv_batch_options_t *options);
+
 /* Sizes of the compiled program and the engine's launch count. Any pointer may be NULL. */
 SV_API sv_status_t sv_batch_info(sv_batch_t b, int *n_items, int *n_stages, int *n_ops,
                                  uint64_t *state_amps, uint64_t *launches);

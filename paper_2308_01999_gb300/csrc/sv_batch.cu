@@ -217,16 +217,16 @@ void emit_window(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vecto
     b->ops.push_back(op);
 }
 
-// The ops of one stage, in order. With `windows`, runs of small ops go into
-// windows of at most kBatchWinQubits qubits -- fewer when the tile is small, so
+// The ops of one stage, in order. With window_qubits >= 2, runs of small ops go
+// into windows of at most that many qubits -- fewer when the tile is small, so
 // that the 2^(T - w) amplitude groups still give every thread of the CTA work
 // -- chosen by the same commutation-aware greedy rule as gate fusion: an op
 // joins the window, at or after the last item touching its qubits, that grows
 // least while staying within the width.
 void emit_stage(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vector<int> &ids, uint64_t lm, int T,
-                bool windows) {
-    int wmax = std::min(svk::kBatchWinQubits, T - 9);
-    if (!windows || wmax < 2) {
+                int window_qubits) {
+    const int wmax = std::min(window_qubits, T - 9);
+    if (wmax < 2) {
         for (int i : ids) emit_op(b, qops[i], lm);
         return;
     }
@@ -264,7 +264,8 @@ void emit_stage(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vector
             if ((qo.qmask >> q) & 1u) last[q] = best;
     }
     for (const WItem &w : items) {
-        if (!w.win || w.ops.size() == 1 || w.q == 0)
+        // a window needs at least 2 qubits (the kernel instantiates 2..4) and 2 ops
+        if (!w.win || w.ops.size() == 1 || popc64(w.q) < 2)
             for (int i : w.ops) emit_op(b, qops[i], lm);
         else
             emit_window(b, qops, w.ops, w.q, lm);
@@ -296,8 +297,18 @@ SV_API sv_status_t sv_batch_destroy(sv_batch_t b) {
 
 SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, int n_items, const sv_gate_t *gates,
                                     int n_gates_total, const int *paulis, int fusion_width) {
+    const sv_batch_options_t opt{fusion_width, svk::kBatchWinQubits};
+    return sv_batch_compile_ex(b, items, n_items, gates, n_gates_total, paulis, &opt);
+}
+
+SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *items, int n_items,
+                                       const sv_gate_t *gates, int n_gates_total, const int *paulis,
+                                       const sv_batch_options_t *options) {
+    if (!options) return SV_ERR_INVALID_ARGUMENT;
+    const int fusion_width = options->fusion_width, window_qubits = options->window_qubits;
     if (!b || (!items && n_items > 0) || n_items < 0 || fusion_width < 1 || fusion_width > 4 ||
-        (n_gates_total > 0 && !gates) || n_gates_total < 0)
+        (n_gates_total > 0 && !gates) || n_gates_total < 0 || window_qubits < 0 || window_qubits == 1 ||
+        window_qubits > svk::kBatchWinQubits)
         return SV_ERR_INVALID_ARGUMENT;
     b->compiled = false;
     b->items.clear();
@@ -386,11 +397,11 @@ SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, 
             const size_t pool0 = b->pool.size(), ops0 = b->ops.size();
             // windows need the stage's matrices staged in shared memory; if they would
             // not fit, the stage is emitted again op by op
-            emit_stage(b, qops, st.ops, lm, T, true);
+            emit_stage(b, qops, st.ops, lm, T, window_qubits);
             if ((int)(b->pool.size() - pool0) > svk::kBatchStageMat) {
                 b->pool.resize(pool0);
                 b->ops.resize(ops0);
-                emit_stage(b, qops, st.ops, lm, T, false);
+                emit_stage(b, qops, st.ops, lm, T, 0);
             }
             bs.op_end = (int)b->ops.size();
             bs.pool_begin = bs.op_end > bs.op_begin ? (int)b->ops[bs.op_begin].mat : (int)b->pool.size();

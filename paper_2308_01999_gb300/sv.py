@@ -43,7 +43,7 @@ EXPORTED = [
     "sv_batch_create", "sv_batch_destroy", "sv_batch_compile", "sv_batch_info", "sv_batch_launch",
     "sv_batch_results", "sv_swap_index_bits", "sv_apply_pauli_rotation", "sv_sample",
     "sv_check_bounded_wait", "sv_apply_fused_ex", "sv_fuse_plan_ex", "sv_copy_from_host_async",
-    "sv_copy_to_host_async",
+    "sv_copy_to_host_async", "sv_batch_compile_ex",
 ]
 
 
@@ -93,6 +93,7 @@ def lib():
             "sv_expectation_pauli_noalloc": [C.c_int, C.c_int, _VP, _VP, _I, _I, C.c_int, C.c_int, _D],
             "sv_batch_create": [_VP, C.POINTER(_VP)], "sv_batch_destroy": [_VP],
             "sv_batch_compile": [_VP, _VP, C.c_int, _VP, C.c_int, _I, C.c_int],
+            "sv_batch_compile_ex": [_VP, _VP, C.c_int, _VP, C.c_int, _I, _VP],
             "sv_batch_info": [_VP, _I, _I, _I, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
             "sv_batch_launch": [_VP, C.c_int, _VP, C.c_int],
             "sv_batch_results": [_VP, _D, C.c_int],
@@ -495,6 +496,18 @@ def sv_batch_compile(b: int, items: np.ndarray, gate_rec: np.ndarray, paulis: np
                                   int(fusion_width)), "sv_batch_compile")
 
 
+def sv_batch_compile_ex(b: int, items: np.ndarray, gate_rec: np.ndarray, paulis: np.ndarray, fusion_width: int,
+                        window_qubits: int):
+    """sv_batch_compile with the register-window width (0, 2, 3 or 4) as an option."""
+    items = np.ascontiguousarray(items, dtype=ITEM_DTYPE)
+    gate_rec = np.ascontiguousarray(gate_rec, dtype=GATE_DTYPE)
+    paulis = np.ascontiguousarray(paulis, dtype=np.int32).reshape(-1)
+    opt = (C.c_int * 2)(int(fusion_width), int(window_qubits))
+    _check(lib().sv_batch_compile_ex(_VP(b), _VP(items.ctypes.data), int(items.size), _VP(gate_rec.ctypes.data),
+                                     int(gate_rec.size), paulis.ctypes.data_as(_I) if paulis.size else None,
+                                     C.cast(opt, _VP)), "sv_batch_compile_ex")
+
+
 def sv_batch_info(b: int) -> dict:
     ni, ns, no = C.c_int(), C.c_int(), C.c_int()
     amps, launches = C.c_uint64(), C.c_uint64()
@@ -528,7 +541,7 @@ class Batch:
         self.handle = sv_batch_create(ptr)
         self._keep = None
 
-    def compile(self, states, fusion_width: int = 2):
+    def compile(self, states, fusion_width: int = 2, window_qubits: int = 4):
         items = np.zeros(len(states), dtype=ITEM_DTYPE)
         all_gates, pls = [], []
         g0 = p0 = o0 = 0
@@ -544,7 +557,7 @@ class Batch:
             a0 += 1 << n
         rec, buf = pack_gates(all_gates)
         pl = np.concatenate(pls) if pls else np.zeros(0, np.int32)
-        sv_batch_compile(self.handle, items, rec, pl, fusion_width)
+        sv_batch_compile_ex(self.handle, items, rec, pl, fusion_width, window_qubits)
         self._keep = (items, rec, buf, pl)
         self.n_out = o0
         self.state_amps = a0

@@ -55,6 +55,12 @@ def test_compile_on_host_only(svmod):
     ans = gen.ansatz_circuit(14, 3, rng)
     w = sv.Batch()
     assert w.compile([(14, ans, np.zeros((0, 14)))], 1)["ops"] < len(ans) / 3
+    # the window width is an option: no windows leave one op per (fused) gate
+    plain = w.compile([(14, ans, np.zeros((0, 14)))], 1, window_qubits=0)["ops"]
+    assert plain > 2 * w.compile([(14, ans, np.zeros((0, 14)))], 1, window_qubits=3)["ops"]
+    for bad in (1, 5, -1):
+        with pytest.raises(sv.SvError):
+            w.compile([(14, ans, np.zeros((0, 14)))], 1, window_qubits=bad)
     w.close()
     with pytest.raises(sv.SvError):
         sv.Batch().compile([(3, [gen.Gate((3,), np.eye(2))], np.zeros((0, 3)))], 2)
@@ -66,14 +72,14 @@ def test_compile_on_host_only(svmod):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("width", [1, 2, 3, 4])
-def test_batch_matches_oracle(svmod, width):
+@pytest.mark.parametrize("width,window", [(1, 4), (2, 4), (3, 4), (4, 4), (1, 0), (2, 2), (1, 3)])
+def test_batch_matches_oracle(svmod, width, window):
     import torch
     sv = svmod
     sizes = [1, 2, 5, 10, 12, 13, 14, 15, 16, 17, 18, 4, 11, 14, 16]
     states = _mixed_states(10 + width, sizes)
     b = sv.Batch(torch.cuda.current_stream())
-    b.compile(states, fusion_width=width)
+    b.compile(states, fusion_width=width, window_qubits=window)
     buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
     b.launch(buf, keep_states=True)
     res = b.results()
