@@ -65,7 +65,11 @@ void grow(Item &b, const std::vector<int> &extra) {
     b.qubits.insert(b.qubits.end(), extra.begin(), extra.end());
 }
 
-// B <- G B, G the gate embedded in the block's basis
+// B <- G B, G the gate embedded in the block's basis. G mixes, within each
+// group of block rows that differ only in the gate's target bits (and satisfy
+// its controls), the rows base | off[l]; each new row is the sum over l of
+// G[j][l] times row l, taken in ascending l -- the same sums, in the same order,
+// as applying G to every column, but on contiguous rows.
 void absorb(Item &b, const sv_gate_t &g) {
     std::vector<int> extra;
     for (int t = 0; t < g.n_targets + g.n_controls; ++t) {
@@ -74,21 +78,36 @@ void absorb(Item &b, const sv_gate_t &g) {
     }
     grow(b, extra);
     const int s = (int)b.qubits.size();
-    int lt[SV_MAX_TARGETS], lc[SV_MAX_CONTROLS], cv[SV_MAX_CONTROLS];
-    for (int t = 0; t < g.n_targets; ++t) lt[t] = local_index(b.qubits, g.targets[t]);
-    for (int t = 0; t < g.n_controls; ++t) {
-        lc[t] = local_index(b.qubits, g.controls[t]);
-        cv[t] = g.control_values[t] ? 1 : 0;
-    }
     const uint64_t d = 1ull << s, D = 1ull << g.n_targets;
-    std::vector<cd> gm(D * D);
+    uint64_t tmask = 0, cmask = 0, cwant = 0;
+    uint64_t off[64];
+    for (uint64_t j = 0; j < D; ++j) off[j] = 0;
+    for (int t = 0; t < g.n_targets; ++t) {
+        const uint64_t bit = 1ull << local_index(b.qubits, g.targets[t]);
+        tmask |= bit;
+        for (uint64_t j = 0; j < D; ++j)
+            if ((j >> t) & 1) off[j] |= bit;
+    }
+    for (int t = 0; t < g.n_controls; ++t) {
+        const uint64_t bit = 1ull << local_index(b.qubits, g.controls[t]);
+        cmask |= bit;
+        if (g.control_values[t]) cwant |= bit;
+    }
+    std::vector<cd> gm(D * D), tmp(D * d);
     for (uint64_t i = 0; i < D * D; ++i) gm[i] = cd(g.matrix[2 * i], g.matrix[2 * i + 1]);
-    // apply to each column of B (column c = B[:, c])
-    std::vector<cd> col(d);
-    for (uint64_t c = 0; c < d; ++c) {
-        for (uint64_t r = 0; r < d; ++r) col[r] = b.m[r * d + c];
-        apply_small(col.data(), s, lt, g.n_targets, lc, cv, g.n_controls, gm.data());
-        for (uint64_t r = 0; r < d; ++r) b.m[r * d + c] = col[r];
+    for (uint64_t base = 0; base < d; ++base) {
+        if ((base & tmask) || (base & cmask) != cwant) continue;
+        for (uint64_t j = 0; j < D; ++j) {
+            cd *out = &tmp[j * d];
+            for (uint64_t c = 0; c < d; ++c) out[c] = 0;
+            for (uint64_t l = 0; l < D; ++l) {
+                const cd m = gm[j * D + l];
+                const cd *row = &b.m[(base | off[l]) * d];
+                for (uint64_t c = 0; c < d; ++c) out[c] += m * row[c];
+            }
+        }
+        for (uint64_t j = 0; j < D; ++j)
+            std::copy(&tmp[j * d], &tmp[j * d] + d, &b.m[(base | off[j]) * d]);
     }
     ++b.n_gates;
 }
