@@ -617,6 +617,19 @@ def run_batch(args):
         flop = sum(6 * n * 16 * (1 << n) for n, _, _ in states)
         out["fp32_flop"] = flop
         out["batched_tflops"] = round(flop / (tune[best]["ms"] * 1e-3) / 1e12, 2)
+        # FP32 ALU roofline: 128 FP32 lanes per SM, one FMA (2 flop) each per clock,
+        # at the maximum SM clock
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = 2070.0
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pk):
+            with open(pk) as f:
+                sm_mhz = float(json.load(f).get("sm_max_mhz", sm_mhz))
+        fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+        out["roofline"] = {"bound": "alu", "kernel": "k_batch", "achieved": out["batched_tflops"],
+                           "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                           "frac": round(out["batched_tflops"] / fp32_peak, 3), "traffic": None,
+                           "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"}
     out["generation_s"] = round(t_gen, 1)
     print(json.dumps(out))
 

@@ -36,11 +36,21 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 // low four bits agree whenever the targets cover bits 0..3 -- all in one bank
 // pair. Mixing bits 4..7 into the bank index spreads them; runs of consecutive
 // amplitudes stay conflict free (each half-warp XORs one constant).
+// The map is linear over XOR, and a group's base and its member offsets have
+// disjoint bits, so sw(base | off) = sw(base) ^ sw(off): the offsets are
+// swizzled once per op and every access costs one XOR.
 __device__ __forceinline__ uint32_t sw(uint32_t a) { return a ^ ((a >> 4) & 15u); }
+// the amplitude at a swizzled byte offset of the tile (one XOR per access)
+__device__ __forceinline__ float2 &at8(float2 *tile, uint32_t byte_off) {
+    return *reinterpret_cast<float2 *>(reinterpret_cast<char *>(tile) + byte_off);
+}
 
+// (unrolled over the twelve slots with constant indices, so that op.p stays in
+// registers; the exit is uniform)
 __device__ __forceinline__ uint32_t insert_zeros_local(uint32_t g, const BOp &op) {
-#pragma unroll 1
-    for (int i = 0; i < op.np; ++i) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        if (i >= op.np) break;
         const uint32_t lo = g & ((1u << op.p[i]) - 1u);
         g = ((g ^ lo) << 1) | lo;
     }
@@ -64,17 +74,17 @@ __device__ void op_dense(float2 *tile, const BOp &op, const float2 *msh, int T) 
     const int ngroups = 1 << (T - op.np);
     uint32_t off[D];
 #pragma unroll
-    for (int j = 0; j < D; ++j) off[j] = member_off<K>(j, op);
+    for (int j = 0; j < D; ++j) off[j] = sw(member_off<K>(j, op)) << 3;
     float2 mreg[kRegMat ? D * D : 1];
     if constexpr (kRegMat) {
 #pragma unroll
         for (int i = 0; i < D * D; ++i) mreg[i] = msh[i];
     }
     for (int g = threadIdx.x; g < ngroups; g += kT) {
-        const uint32_t base = insert_zeros_local((uint32_t)g, op);
+        const uint32_t base = sw(insert_zeros_local((uint32_t)g, op)) << 3;
         float2 v[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) v[j] = tile[sw(base | off[j])];
+        for (int j = 0; j < D; ++j) v[j] = at8(tile, base ^ off[j]);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             float2 acc = make_float2(0.f, 0.f);
@@ -86,7 +96,7 @@ __device__ void op_dense(float2 *tile, const BOp &op, const float2 *msh, int T) 
                 acc.y = __fmaf_rn(m.x, v[l].y, acc.y);
                 acc.y = __fmaf_rn(m.y, v[l].x, acc.y);
             }
-            tile[sw(base | off[j])] = acc;
+            at8(tile, base ^ off[j]) = acc;
         }
     }
 }
@@ -99,16 +109,16 @@ __device__ void op_perm(float2 *tile, const BOp &op, const float2 *msh, int T) {
     uint32_t src[D], dst[D];
 #pragma unroll
     for (int l = 0; l < D; ++l) {
-        src[l] = member_off<K>(l, op);
-        dst[l] = member_off<K>(__float_as_int(msh[D + l].x), op);
+        src[l] = sw(member_off<K>(l, op));
+        dst[l] = sw(member_off<K>(__float_as_int(msh[D + l].x), op));
     }
     for (int g = threadIdx.x; g < ngroups; g += kT) {
-        const uint32_t base = insert_zeros_local((uint32_t)g, op);
+        const uint32_t base = sw(insert_zeros_local((uint32_t)g, op));
         float2 v[D];
 #pragma unroll
-        for (int l = 0; l < D; ++l) v[l] = tile[sw(base | src[l])];
+        for (int l = 0; l < D; ++l) v[l] = tile[base ^ src[l]];
 #pragma unroll
-        for (int l = 0; l < D; ++l) tile[sw(base | dst[l])] = cmulf(msh[l], v[l]);
+        for (int l = 0; l < D; ++l) tile[base ^ dst[l]] = cmulf(msh[l], v[l]);
     }
 }
 
@@ -118,29 +128,57 @@ __device__ void op_diag(float2 *tile, const BOp &op, const float2 *msh, int T) {
     for (int g = threadIdx.x; g < namps; g += kT) {
         const uint32_t a = insert_zeros_local((uint32_t)g, op);
         int j = 0;
-        for (int t = 0; t < op.k; ++t) j |= (int)((a >> op.t[t]) & 1u) << t;
-        tile[sw(a)] = cmulf(msh[j], tile[sw(a)]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (t < op.k) j |= (int)((a >> op.t[t]) & 1u) << t;
+        const uint32_t sa = sw(a);
+        tile[sa] = cmulf(msh[j], tile[sa]);
     }
 }
 
 // ---- windows: a run of small ops on 2^W amplitudes held in registers ----
-// Template arguments fix every register index; the run-time target bits select
-// the instantiation. Control conditions ((r & cm) == cv) are uniform across the
-// CTA, so they only predicate.
-template <int W, int B>
+// Template arguments fix every register index; the host-computed case selects
+// the instantiation. Run-time control conditions ((r & cm) == cv) are uniform
+// across the CTA, so they only predicate; uncontrolled ops (CTRL false) and
+// plain exchanges carry none.
+// One 2x2 product on the pair (a, c) -> (o0, o1) = (m00 a + m01 c, m10 a + m11 c).
+// Each output component is finished last with the input component whose
+// register it takes over (x0 <- a.x, y0 <- a.y, x1 <- c.x, y1 <- c.y, or the
+// exchanged assignment when SWAPPED), after every partial sum has been formed:
+// each register dies exactly where its result is written, so the results
+// need no copies back into the fixed registers of v[].
+template <bool SWAPPED>
+__device__ __forceinline__ void pair2x2(float2 &a, float2 &c, float2 m00, float2 m01, float2 m10, float2 m11) {
+    if constexpr (!SWAPPED) {
+        const float p0 = __fmaf_rn(m01.x, c.x, __fmaf_rn(-m00.y, a.y, -m01.y * c.y));   // o0.x without a.x
+        const float p1 = __fmaf_rn(m01.x, c.y, __fmaf_rn(m00.y, a.x, m01.y * c.x));     // o0.y without a.y
+        const float p2 = __fmaf_rn(m10.x, a.x, __fmaf_rn(-m10.y, a.y, -m11.y * c.y));   // o1.x without c.x
+        const float p3 = __fmaf_rn(m10.x, a.y, __fmaf_rn(m10.y, a.x, m11.y * c.x));     // o1.y without c.y
+        a.y = __fmaf_rn(m00.x, a.y, p1);
+        c.x = __fmaf_rn(m11.x, c.x, p2);
+        c.y = __fmaf_rn(m11.x, c.y, p3);
+        a.x = __fmaf_rn(m00.x, a.x, p0);
+    } else {   // o1 into a's registers, o0 into c's
+        const float p0 = __fmaf_rn(m00.x, a.x, __fmaf_rn(-m00.y, a.y, -m01.y * c.y));   // o0.x without c.x
+        const float p1 = __fmaf_rn(m00.x, a.y, __fmaf_rn(m00.y, a.x, m01.y * c.x));     // o0.y without c.y
+        const float p2 = __fmaf_rn(m11.x, c.x, __fmaf_rn(-m10.y, a.y, -m11.y * c.y));   // o1.x without a.x
+        const float p3 = __fmaf_rn(m11.x, c.y, __fmaf_rn(m10.y, a.x, m11.y * c.x));     // o1.y without a.y
+        c.y = __fmaf_rn(m01.x, c.y, p1);
+        a.x = __fmaf_rn(m10.x, a.x, p2);
+        a.y = __fmaf_rn(m10.x, a.y, p3);
+        c.x = __fmaf_rn(m01.x, c.x, p0);
+    }
+}
+
+template <int W, int B, bool CTRL>
 __device__ __forceinline__ void win_dense1(float2 (&v)[1 << W], const float2 *m, uint32_t cm, uint32_t cv) {
     if constexpr (B < W) {
         const float2 m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
 #pragma unroll
         for (int r = 0; r < (1 << W); ++r) {
             if (r & (1 << B)) continue;
-            if (((uint32_t)r & cm) != cv) continue;
-            const float2 a = v[r], c = v[r | (1 << B)];
-            v[r] = make_float2(__fmaf_rn(m00.x, a.x, __fmaf_rn(-m00.y, a.y, __fmaf_rn(m01.x, c.x, -m01.y * c.y))),
-                               __fmaf_rn(m00.x, a.y, __fmaf_rn(m00.y, a.x, __fmaf_rn(m01.x, c.y, m01.y * c.x))));
-            v[r | (1 << B)] =
-                make_float2(__fmaf_rn(m10.x, a.x, __fmaf_rn(-m10.y, a.y, __fmaf_rn(m11.x, c.x, -m11.y * c.y))),
-                            __fmaf_rn(m10.x, a.y, __fmaf_rn(m10.y, a.x, __fmaf_rn(m11.x, c.y, m11.y * c.x))));
+            if (CTRL && ((uint32_t)r & cm) != cv) continue;
+            pair2x2<false>(v[r], v[r | (1 << B)], m00, m01, m10, m11);
         }
     }
 }
@@ -160,13 +198,64 @@ __device__ __forceinline__ void win_swap1(float2 (&v)[1 << W], const float2 *m, 
     }
 }
 
-template <int W, int B0, int B1>
+// a 2x2 on bit B followed by the exchange across bit T where bit C == CV
+// (B is C or T): the products are written straight into the exchanged registers
+template <int W, int B, int C, int T, int CV>
+__device__ __forceinline__ void win_dense1_cx(float2 (&v)[1 << W], const float2 *m) {
+    if constexpr (B < W && C < W && T < W && B == T) {
+        // the exchange stays within each pair: its outputs trade registers
+        const float2 m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) {
+            if (r & (1 << B)) continue;
+            if (((r >> C) & 1) == CV)
+                pair2x2<true>(v[r], v[r | (1 << B)], m00, m01, m10, m11);
+            else
+                pair2x2<false>(v[r], v[r | (1 << B)], m00, m01, m10, m11);
+        }
+    } else if constexpr (B < W && C < W && T < W) {
+        const float2 m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
+        float2 o[1 << W];
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) {
+            if (r & (1 << B)) continue;
+            const float2 a = v[r], c = v[r | (1 << B)];
+            o[r] = make_float2(__fmaf_rn(m00.x, a.x, __fmaf_rn(-m00.y, a.y, __fmaf_rn(m01.x, c.x, -m01.y * c.y))),
+                               __fmaf_rn(m00.x, a.y, __fmaf_rn(m00.y, a.x, __fmaf_rn(m01.x, c.y, m01.y * c.x))));
+            o[r | (1 << B)] =
+                make_float2(__fmaf_rn(m10.x, a.x, __fmaf_rn(-m10.y, a.y, __fmaf_rn(m11.x, c.x, -m11.y * c.y))),
+                            __fmaf_rn(m10.x, a.y, __fmaf_rn(m10.y, a.x, __fmaf_rn(m11.x, c.y, m11.y * c.x))));
+        }
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) v[((r >> C) & 1) == CV ? (r ^ (1 << T)) : r] = o[r];
+    }
+}
+
+// members exchanged across bit B (C < 0) or where window bit C equals CV: a
+// renaming of registers, no arithmetic, but moves where the cases rejoin
+template <int W, int B, int C, int CV>
+__device__ __forceinline__ void win_xswap(float2 (&v)[1 << W]) {
+    if constexpr (B < W && C < W) {
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) {
+            if (r & (1 << B)) continue;
+            if constexpr (C >= 0) {
+                if (((r >> C) & 1) != CV) continue;
+            }
+            const float2 a = v[r];
+            v[r] = v[r | (1 << B)];
+            v[r | (1 << B)] = a;
+        }
+    }
+}
+
+template <int W, int B0, int B1, bool CTRL>
 __device__ __forceinline__ void win_dense2(float2 (&v)[1 << W], const float2 *m, uint32_t cm, uint32_t cv) {
     if constexpr (B0 < B1 && B1 < W) {
 #pragma unroll
         for (int r = 0; r < (1 << W); ++r) {
             if (r & ((1 << B0) | (1 << B1))) continue;
-            if (((uint32_t)r & cm) != cv) continue;
+            if (CTRL && ((uint32_t)r & cm) != cv) continue;
             const int o[4] = {r, r | (1 << B0), r | (1 << B1), r | (1 << B0) | (1 << B1)};
             float2 a[4];
 #pragma unroll
@@ -199,62 +288,79 @@ __device__ __forceinline__ void win_diag(float2 (&v)[1 << W], const float2 *m, i
     }
 }
 
+// the window's groups: zero bits inserted at its W positions
+template <int W>
+__device__ __forceinline__ uint32_t insert_zeros_win(uint32_t g, const BOp &op) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const uint32_t lo = g & ((1u << op.p[i]) - 1u);
+        g = ((g ^ lo) << 1) | lo;
+    }
+    return g;
+}
+
+#define SV_WC_BIT(B)                                                              \
+    case WC_DENSE1 + B: win_dense1<W, B, false>(v, m, cm, cv); break;            \
+    case WC_DENSE1C + B: win_dense1<W, B, true>(v, m, cm, cv); break;            \
+    case WC_SWAP1 + B: win_swap1<W, B>(v, m, cm, cv); break;                     \
+    case WC_XSWAP + B: win_xswap<W, B, -1, 0>(v); break;
+#define SV_WC_PAIR(B0, B1)                                                        \
+    case WC_DENSE2 + wc_pair(B0, B1): win_dense2<W, B0, B1, false>(v, m, cm, cv); break; \
+    case WC_DENSE2C + wc_pair(B0, B1): win_dense2<W, B0, B1, true>(v, m, cm, cv); break;
+#define SV_WC_D1CX(C, T)                                                                             \
+    case WC_D1CX + wc_opair(C, T) * 2: win_dense1_cx<W, T, C, T, 0>(v, m); break;                   \
+    case WC_D1CX + wc_opair(C, T) * 2 + 1: win_dense1_cx<W, T, C, T, 1>(v, m); break;               \
+    case WC_D1CX + (12 + wc_opair(C, T)) * 2: win_dense1_cx<W, C, C, T, 0>(v, m); break;            \
+    case WC_D1CX + (12 + wc_opair(C, T)) * 2 + 1: win_dense1_cx<W, C, C, T, 1>(v, m); break;
+#define SV_WC_CX(B, C)                                                            \
+    case WC_CXSWAP + (4 * B + C) * 2: win_xswap<W, B, C, 0>(v); break;           \
+    case WC_CXSWAP + (4 * B + C) * 2 + 1: win_xswap<W, B, C, 1>(v); break;
+
 template <int W>
 __device__ void op_window(float2 *tile, const BOp &op, const float2 *blk, int T) {
     constexpr int D = 1 << W;
     const int ngroups = 1 << (T - W);
     const int nsub = op.k;
+    // swizzled byte offsets of the members: XOR prefixes of the per-bit ones
     uint32_t off[D];
+    off[0] = 0;
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-        uint32_t o = 0;
-#pragma unroll
-        for (int t = 0; t < W; ++t)
-            if ((j >> t) & 1) o |= 1u << op.p[t];
-        off[j] = o;
+    for (int j = 1; j < D; ++j) {
+        const int t = 31 - __clz(j);
+        off[j] = off[j ^ (1 << t)] ^ (sw(1u << op.p[t]) << 3);
     }
     for (int g = threadIdx.x; g < ngroups; g += kT) {
-        const uint32_t base = insert_zeros_local((uint32_t)g, op);
+        const uint32_t base = sw(insert_zeros_win<W>((uint32_t)g, op)) << 3;
         float2 v[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) v[j] = tile[sw(base | off[j])];
+        for (int j = 0; j < D; ++j) v[j] = at8(tile, base ^ off[j]);
         for (int s = 0; s < nsub; ++s) {
             const float2 h0 = blk[2 * s], h1 = blk[2 * s + 1];
-            const uint32_t hx = __float_as_uint(h0.x), hy = __float_as_uint(h0.y);
-            const int kind = hx & 0xff, b0 = (hx >> 8) & 0xff, b1 = (hx >> 16) & 0xff, nd = hx >> 24;
+            const uint32_t hy = __float_as_uint(h0.y);
             const uint32_t cm = hy & 0xff, cv = (hy >> 8) & 0xff;
             const float2 *m = blk + __float_as_uint(h1.x);
-            if (kind == BSUB_DENSE1) {
-                switch (b0) {
-                case 0: win_dense1<W, 0>(v, m, cm, cv); break;
-                case 1: win_dense1<W, 1>(v, m, cm, cv); break;
-                case 2: win_dense1<W, 2>(v, m, cm, cv); break;
-                default: win_dense1<W, 3>(v, m, cm, cv); break;
-                }
-            } else if (kind == BSUB_DENSE2) {
-                switch (b0 * 4 + b1) {
-                case 1: win_dense2<W, 0, 1>(v, m, cm, cv); break;
-                case 2: win_dense2<W, 0, 2>(v, m, cm, cv); break;
-                case 3: win_dense2<W, 0, 3>(v, m, cm, cv); break;
-                case 6: win_dense2<W, 1, 2>(v, m, cm, cv); break;
-                case 7: win_dense2<W, 1, 3>(v, m, cm, cv); break;
-                default: win_dense2<W, 2, 3>(v, m, cm, cv); break;
-                }
-            } else if (kind == BSUB_SWAP1) {
-                switch (b0) {
-                case 0: win_swap1<W, 0>(v, m, cm, cv); break;
-                case 1: win_swap1<W, 1>(v, m, cm, cv); break;
-                case 2: win_swap1<W, 2>(v, m, cm, cv); break;
-                default: win_swap1<W, 3>(v, m, cm, cv); break;
-                }
-            } else {
-                win_diag<W>(v, m, nd, b0, b1, cm, cv);
+            switch (hy >> 16) {
+                SV_WC_BIT(0) SV_WC_BIT(1) SV_WC_BIT(2) SV_WC_BIT(3)
+                SV_WC_PAIR(0, 1) SV_WC_PAIR(0, 2) SV_WC_PAIR(0, 3) SV_WC_PAIR(1, 2) SV_WC_PAIR(1, 3) SV_WC_PAIR(2, 3)
+                SV_WC_CX(0, 1) SV_WC_CX(0, 2) SV_WC_CX(0, 3) SV_WC_CX(1, 0) SV_WC_CX(1, 2) SV_WC_CX(1, 3)
+                SV_WC_CX(2, 0) SV_WC_CX(2, 1) SV_WC_CX(2, 3) SV_WC_CX(3, 0) SV_WC_CX(3, 1) SV_WC_CX(3, 2)
+                SV_WC_D1CX(0, 1) SV_WC_D1CX(0, 2) SV_WC_D1CX(0, 3) SV_WC_D1CX(1, 0) SV_WC_D1CX(1, 2) SV_WC_D1CX(1, 3)
+                SV_WC_D1CX(2, 0) SV_WC_D1CX(2, 1) SV_WC_D1CX(2, 3) SV_WC_D1CX(3, 0) SV_WC_D1CX(3, 1) SV_WC_D1CX(3, 2)
+            default: {
+                const uint32_t hx = __float_as_uint(h0.x);
+                win_diag<W>(v, m, hx >> 24, (hx >> 8) & 0xff, (hx >> 16) & 0xff, cm, cv);
+            }
             }
         }
 #pragma unroll
-        for (int j = 0; j < D; ++j) tile[sw(base | off[j])] = v[j];
+        for (int j = 0; j < D; ++j) at8(tile, base ^ off[j]) = v[j];
     }
 }
+
+#undef SV_WC_BIT
+#undef SV_WC_PAIR
+#undef SV_WC_CX
+#undef SV_WC_D1CX
 
 __device__ double block_sum(double v, double *red) {
 #pragma unroll

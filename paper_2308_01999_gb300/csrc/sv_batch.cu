@@ -162,13 +162,53 @@ bool windowable(const QOp &qo, int w) {
     return qo.kind == svk::BOP_DENSE || qo.kind == svk::BOP_DIAG || qo.kind == svk::BOP_PERM;
 }
 
+bool plain_dense1(const QOp &qo) { return qo.kind == svk::BOP_DENSE && qo.t.size() == 1 && qo.c.empty(); }
+bool plain_cx(const QOp &qo) {
+    return qo.kind == svk::BOP_PERM && qo.t.size() == 1 && qo.c.size() == 1 && qo.data[0] == cd(1, 0) &&
+           qo.data[1] == cd(1, 0);
+}
+
+// Pairs each plain controlled exchange (CNOT, control value 0 or 1) with an
+// uncontrolled one-qubit dense op on one of its qubits, where the ops between
+// them all commute with one of the two (act on other qubits): the dense op
+// then writes its outputs straight into the exchanged registers. Returns the
+// window's items in a valid order, each {op, exchange or -1}.
+std::vector<std::pair<int, int>> pair_exchanges(const std::vector<QOp> &qops, const std::vector<int> &idx) {
+    std::vector<std::pair<int, int>> it;
+    for (int i : idx) it.push_back({i, -1});
+    for (size_t j = 0; j < it.size(); ++j) {
+        const QOp &cx = qops[it[j].first];
+        if (it[j].second >= 0 || !plain_cx(cx)) continue;
+        uint64_t between = 0;
+        for (size_t i = j; i-- > 0;) {
+            const QOp &o = qops[it[i].first];
+            if (it[i].second < 0 && plain_dense1(o) && (o.qmask & cx.qmask)) {
+                if ((between & o.qmask) == 0) {            // the dense op moves forward to the exchange
+                    it[j] = {it[i].first, it[j].first};
+                    it.erase(it.begin() + (long)i);
+                    --j;
+                } else if ((between & cx.qmask) == 0) {    // the exchange moves back to the dense op
+                    it[i].second = it[j].first;
+                    it.erase(it.begin() + (long)j);
+                    --j;
+                }
+                break;
+            }
+            between |= o.qmask;
+            if (it[i].second >= 0) between |= qops[it[i].second].qmask;
+        }
+    }
+    return it;
+}
+
 // a window: the ops (at most 2 targets each, all on the local positions `wq`)
 // applied one after another to 2^|wq| amplitudes held in registers
-void emit_window(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vector<int> &idx, uint64_t wq,
+void emit_window(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vector<int> &idx_in, uint64_t wq,
                  uint64_t lm) {
+    const std::vector<std::pair<int, int>> items = pair_exchanges(qops, idx_in);
     svk::BOp op{};
     op.kind = svk::BOP_WIN;
-    op.k = (uint8_t)idx.size();
+    op.k = (uint8_t)items.size();
     std::vector<int> wl;                    // window bit i <-> local position wl[i]
     for (int q = 0; q < 64; ++q)
         if ((wq >> q) & 1u) wl.push_back(local_pos(lm, q));
@@ -182,9 +222,9 @@ void emit_window(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vecto
         return (int)(std::find(wl.begin(), wl.end(), l) - wl.begin());
     };
     const size_t hdr = b->pool.size();
-    b->pool.resize(hdr + 2 * idx.size());
-    for (size_t s = 0; s < idx.size(); ++s) {
-        const QOp &qo = qops[idx[s]];
+    b->pool.resize(hdr + 2 * items.size());
+    for (size_t s = 0; s < items.size(); ++s) {
+        const QOp &qo = qops[items[s].first];
         uint32_t cm = 0, cv = 0;
         for (size_t i = 0; i < qo.c.size(); ++i) {
             cm |= 1u << wbit(qo.c[i]);
@@ -193,16 +233,35 @@ void emit_window(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vecto
         const int k = (int)qo.t.size(), D = 1 << k;
         const int b0 = k > 0 ? wbit(qo.t[0]) : 0, b1 = k > 1 ? wbit(qo.t[1]) : 0;
         const uint32_t moff = (uint32_t)(b->pool.size() - hdr);
-        uint32_t kind;
+        uint32_t kind, wc;
         if (qo.kind == svk::BOP_DIAG) {
             kind = svk::BSUB_DIAG;
+            wc = svk::WC_DIAG;
             for (int j = 0; j < D; ++j) b->pool.push_back(make_float2((float)qo.data[j].real(), (float)qo.data[j].imag()));
         } else if (qo.kind == svk::BOP_PERM && k == 1) {
-            // the only non-diagonal one-target permutation: member l goes to 1 - l times f[l]
+            // the only non-diagonal one-target permutation: member l goes to 1 - l times f[l];
+            // with both factors exactly 1 and at most one control it is a plain exchange
             kind = svk::BSUB_SWAP1;
+            const bool plain = qo.data[0] == cd(1, 0) && qo.data[1] == cd(1, 0);
+            if (plain && cm == 0) {
+                wc = svk::WC_XSWAP + b0;
+            } else if (plain && popc64(cm) == 1) {
+                const int c = __builtin_ctz(cm);
+                wc = svk::WC_CXSWAP + (4 * b0 + c) * 2 + ((cv >> c) & 1u);
+            } else {
+                wc = svk::WC_SWAP1 + b0;
+            }
             for (int l = 0; l < 2; ++l) b->pool.push_back(make_float2((float)qo.data[l].real(), (float)qo.data[l].imag()));
         } else {
             kind = k == 1 ? svk::BSUB_DENSE1 : svk::BSUB_DENSE2;
+            if (items[s].second >= 0) {
+                const QOp &cx = qops[items[s].second];
+                const int c = wbit(cx.c[0]), t = wbit(cx.t[0]);
+                wc = svk::WC_D1CX + (uint32_t)(((b0 == t ? 0 : 12) + svk::wc_opair(c, t)) * 2 + (cx.cv[0] ? 1 : 0));
+            } else if (k == 1)
+                wc = (cm ? svk::WC_DENSE1C : svk::WC_DENSE1) + b0;
+            else
+                wc = (cm ? svk::WC_DENSE2C : svk::WC_DENSE2) + svk::wc_pair(b0, b1);
             std::vector<cd> m(D * D, cd(0));
             if (qo.kind == svk::BOP_PERM) {
                 for (int l = 0; l < D; ++l) m[(int)qo.data[D + l].real() * D + l] = qo.data[l];
@@ -211,7 +270,8 @@ void emit_window(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vecto
             }
             for (int i = 0; i < D * D; ++i) b->pool.push_back(make_float2((float)m[i].real(), (float)m[i].imag()));
         }
-        b->pool[hdr + 2 * s] = bits_f2(kind | (uint32_t)b0 << 8 | (uint32_t)b1 << 16 | (uint32_t)k << 24, cm | cv << 8);
+        b->pool[hdr + 2 * s] =
+            bits_f2(kind | (uint32_t)b0 << 8 | (uint32_t)b1 << 16 | (uint32_t)k << 24, cm | cv << 8 | wc << 16);
         b->pool[hdr + 2 * s + 1] = bits_f2(moff, 0);
     }
     b->ops.push_back(op);

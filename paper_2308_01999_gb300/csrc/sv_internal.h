@@ -105,10 +105,28 @@ enum BatchOpKind { BOP_DENSE = 0, BOP_DIAG = 1, BOP_PERM = 2, BOP_WIN = 3 };
 // A window (BOP_WIN) applies a run of small ops to amplitudes held in registers:
 // its np <= kBatchWinQubits local positions p[] span 2^np amplitudes per thread,
 // k is the number of sub-ops, and pool[mat ..] holds k two-entry headers
-// (kind | b0 << 8 | b1 << 16 | nd << 24, control mask | control values << 8,
-// matrix offset from pool[mat], 0) followed by their matrices.
+// (kind | b0 << 8 | b1 << 16 | nd << 24, control mask | control values << 8 |
+// case << 16, matrix offset from pool[mat], 0) followed by their matrices.
 constexpr int kBatchWinQubits = 4;
 enum BatchSubKind { BSUB_DENSE1 = 0, BSUB_DENSE2 = 1, BSUB_DIAG = 2, BSUB_SWAP1 = 3 };
+// The sub-op's case: the kernel jumps on it once, into code whose window bits
+// (and, for plain swaps, whose control) are compile-time constants.
+enum BatchWinCase {
+    WC_DENSE1 = 0,     // + b: 2x2 on window bit b, no control
+    WC_DENSE1C = 4,    // + b: 2x2 where (r & cm) == cv
+    WC_DENSE2 = 8,     // + wc_pair(b0, b1): 4x4 on bits b0 < b1, no control
+    WC_DENSE2C = 14,   // + wc_pair(b0, b1): 4x4 where (r & cm) == cv
+    WC_SWAP1 = 20,     // + b: member l -> 1 - l times f[l], where (r & cm) == cv
+    WC_XSWAP = 24,     // + b: members exchanged (factors exactly 1), no control
+    WC_CXSWAP = 28,    // + (4 b + c) * 2 + v: members exchanged where window bit c == v (c != b)
+    WC_DIAG = 60,      // diagonal, run-time bits and control
+    WC_D1CX = 64,      // + ((s ? 12 : 0) + wc_opair(c, t)) * 2 + v: 2x2 on bit t (s = 0) or c (s = 1),
+                       //   then members exchanged across bit t where bit c == v
+};
+// index of the pair b0 < b1 < 4 among 01 02 03 12 13 23
+constexpr __host__ __device__ int wc_pair(int b0, int b1) { return b0 * (7 - b0) / 2 + (b1 - b0 - 1); }
+// index of the ordered pair (c, t), c != t < 4
+constexpr __host__ __device__ int wc_opair(int c, int t) { return c * 3 + (t > c ? t - 1 : t); }
 
 struct BItem {
     uint64_t state_off;      // amplitude offset of the state

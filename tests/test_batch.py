@@ -19,12 +19,34 @@ def svmod():
 def _mixed_states(seed, sizes, strings=5):
     rng = gen.rng_for(seed)
     states = []
+    x = np.array([[0, 1], [1, 0]], dtype=complex)
+    y = np.array([[0, -1j], [1j, 0]])
     for i, n in enumerate(sizes):
-        if i % 3 == 0:
+        if i % 4 == 0:
             gates = gen.ansatz_circuit(n, 3, rng)
-        elif i % 3 == 1:
+        elif i % 4 == 1:
             gates = gen.layered_random_circuit(n, 3, seed + i, ("cz", "cnot", "crz")) if n >= 2 else \
                 [gen.Gate((0,), gen.haar_su2(rng))]
+        elif i % 4 == 3 and n >= 3:
+            # permutations on a few qubits, so that they share register windows:
+            # X, X controlled on 0 or 1, Toffoli-like with random control values,
+            # controlled Y (factors +-i), and Haar gates in between
+            pool = [int(v) for v in rng.choice(n, min(n, 5), replace=False)]
+            gates = []
+            for _ in range(24):
+                qs = [int(v) for v in rng.choice(pool, 3, replace=False)]
+                kind = int(rng.integers(0, 5))
+                cv = tuple(int(v) for v in rng.integers(0, 2, size=2))
+                if kind == 0:
+                    gates.append(gen.Gate((qs[0],), gen.haar_su2(rng)))
+                elif kind == 1:
+                    gates.append(gen.Gate((qs[0],), x))
+                elif kind == 2:
+                    gates.append(gen.Gate((qs[0],), x, (qs[1],), cv[:1]))
+                elif kind == 3:
+                    gates.append(gen.Gate((qs[0],), x, (qs[1], qs[2]), cv))
+                else:
+                    gates.append(gen.Gate((qs[0],), y, (qs[1],), cv[:1]))
         else:
             gates = []
             for _ in range(12):
