@@ -17,7 +17,7 @@
 // dense k <= 4 (matrix staged in shared memory per op, one thread per group),
 // diagonal (phases on the subspace where the controls hold) and generalized
 // permutation. Pauli expectations are then reduced from shared memory (or
-// from the state in L2 / HBM) with FP32 sums of at most 16 terms per thread
+// from the state in L2 / HBM) with FP32 runs of at most 8 terms per thread
 // and FP64 beyond, block partials summed in a fixed order.
 #include "sv_internal.h"
 
@@ -430,7 +430,20 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
                     for (int l = threadIdx.x; l < L; l += kT)
                         tile[sw(l)] = make_float2((tbase | lo_tab[l & 127] | hi_tab[l >> 7]) == 0u ? 1.f : 0.f, 0.f);
                 } else {
-                    for (int l = threadIdx.x; l < L; l += kT) tile[sw(l)] = sv[tbase | lo_tab[l & 127] | hi_tab[l >> 7]];
+                    // eight gathers in flight per thread before the shared-memory writes
+                    for (int l0 = threadIdx.x; l0 < L; l0 += 8 * kT) {
+                        float2 t8[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int l = l0 + u * kT;
+                            if (l < L) t8[u] = sv[tbase | lo_tab[l & 127] | hi_tab[l >> 7]];
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int l = l0 + u * kT;
+                            if (l < L) tile[sw(l)] = t8[u];
+                        }
+                    }
                 }
                 for (int o = S.op_begin; o < S.op_end; ++o) {
                     const BOp op = ops[o];
@@ -484,31 +497,48 @@ k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_item
             const uint32_t x = (uint32_t)P.x, z = (uint32_t)P.z;
             double acc = 0.0;
             float run = 0.f;
-            int cnt = 0;
             // terms i and i ^ x come from the same pair of loads: w_i = psi_i conj(psi_{i^x}),
             // w_{i^x} = conj(w_i); pairs are enumerated by inserting a zero at the highest
             // bit of x (any set bit would do; the highest keeps a warp's loads contiguous)
+            // kU pairs per iteration, all loads issued before any use (memory-level
+            // parallelism for states read from L2 / HBM; kU = 8 spilled registers);
+            // the FP32 run of at most 8 terms goes into the FP64 sum after every
+            // fourth pair
             const int pb = x ? 31 - __clz(x) : 0;
             const uint32_t npairs = x ? N / 2 : N;
-            for (uint32_t g = threadIdx.x; g < npairs; g += kT) {
-                const uint32_t i = x ? (((g >> pb) << (pb + 1)) | (g & ((1u << pb) - 1u))) : g;
-                const uint32_t j = i ^ x;
-                const float2 a = n == T ? tile[sw(i)] : sv[i];
-                const float2 b = x ? (n == T ? tile[sw(j)] : sv[j]) : a;
-                const float re = a.x * b.x + a.y * b.y, im = a.y * b.x - a.x * b.y;
-                const float ti = P.use_im ? im : re;
-                run += (__popc(i & z) & 1) ? -ti : ti;
-                if (x) {
-                    const float tj = P.use_im ? -im : re;
-                    run += (__popc(j & z) & 1) ? -tj : tj;
+            constexpr int kU = 4;
+            for (uint32_t g0 = threadIdx.x; g0 < npairs; g0 += kU * kT) {
+                float2 a[kU], b[kU];
+                uint32_t ii[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const uint32_t g = g0 + (uint32_t)u * kT;
+                    ii[u] = x ? (((g >> pb) << (pb + 1)) | (g & ((1u << pb) - 1u))) : g;
+                    if (g < npairs) {
+                        const uint32_t j = ii[u] ^ x;
+                        a[u] = n == T ? tile[sw(ii[u])] : sv[ii[u]];
+                        b[u] = x ? (n == T ? tile[sw(j)] : sv[j]) : a[u];
+                    }
                 }
-                if (++cnt == 8) {
-                    acc += (double)run;
-                    run = 0.f;
-                    cnt = 0;
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    if (g0 + (uint32_t)u * kT >= npairs) continue;
+                    const uint32_t i = ii[u], j = i ^ x;
+                    const float re = a[u].x * b[u].x + a[u].y * b[u].y, im = a[u].y * b[u].x - a[u].x * b[u].y;
+                    const float ti = P.use_im ? im : re;
+                    run += (__popc(i & z) & 1) ? -ti : ti;
+                    if (x) {
+                        const float tj = P.use_im ? -im : re;
+                        run += (__popc(j & z) & 1) ? -tj : tj;
+                    }
+                    if ((u & 3) == 3) {
+                        acc += (double)run;
+                        run = 0.f;
+                    }
                 }
+                acc += (double)run;
+                run = 0.f;
             }
-            acc += (double)run;
             const double tot = block_sum(acc, red);
             if (threadIdx.x == 0) out[it.out_begin + s] = (double)P.sign * tot;
         }
