@@ -16,7 +16,11 @@
 // Ops (compiled on the host, exact structure analysis as in sv_apply_matrix):
 // dense k <= 4 (matrix staged in shared memory per op, one thread per group),
 // diagonal (phases on the subspace where the controls hold) and generalized
-// permutation. Pauli expectations are then reduced from shared memory (or
+// permutation; runs of such ops with at most 2 targets on at most 4 local
+// qubits form register windows (op_window): each thread holds the 2^w
+// amplitudes of one group in registers, applies the whole run there through
+// one jump per sub-op into code with constant register indices, and writes
+// them back once. Pauli expectations are then reduced from shared memory (or
 // from the state in L2 / HBM) with FP32 runs of at most 8 terms per thread
 // and FP64 beyond, block partials summed in a fixed order.
 #include "sv_internal.h"

@@ -98,7 +98,9 @@ def test_compile_on_host_only(svmod):
 def test_batch_matches_oracle(svmod, width, window):
     import torch
     sv = svmod
-    sizes = [1, 2, 5, 10, 12, 13, 14, 15, 16, 17, 18, 4, 11, 14, 16]
+    # every fourth state (i % 4 == 3) is the permutation mix; the 15- and
+    # 13-qubit ones run it through 4-qubit register windows
+    sizes = [1, 2, 5, 10, 12, 13, 14, 15, 16, 17, 18, 4, 11, 14, 16, 13, 12, 20]
     states = _mixed_states(10 + width, sizes)
     b = sv.Batch(torch.cuda.current_stream())
     b.compile(states, fusion_width=width, window_qubits=window)
