@@ -344,6 +344,7 @@ SV_API sv_status_t sv_batch_info(sv_batch_t b, int *n_items, int *n_stages, int 
  * memory of at least the largest state_offset + 2^n_qubits complex64
  * amplitudes, 16-byte aligned, caller-owned; states above 14 qubits always use
  * it, smaller ones only with SV_BATCH_KEEP_STATES. dtype must be SV_C64.
+ * A program of no states launches nothing and accepts d_states = NULL.
  * Asynchronous. */
 SV_API sv_status_t sv_batch_launch(sv_batch_t b, sv_dtype_t dtype, void *d_states, int flags);
 

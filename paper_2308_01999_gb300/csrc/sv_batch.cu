@@ -504,9 +504,10 @@ SV_API sv_status_t sv_batch_info(sv_batch_t b, int *n_items, int *n_stages, int 
 }
 
 SV_API sv_status_t sv_batch_launch(sv_batch_t b, sv_dtype_t dtype, void *d_states, int flags) {
-    if (!b || !b->compiled || !d_states || (reinterpret_cast<uintptr_t>(d_states) & 15u)) return SV_ERR_INVALID_ARGUMENT;
+    if (!b || !b->compiled) return SV_ERR_INVALID_ARGUMENT;
     if (dtype != SV_C64) return SV_ERR_NOT_SUPPORTED;
-    if (b->items.empty()) return SV_OK;
+    if (b->items.empty()) return SV_OK;   // nothing to run: d_states may be NULL
+    if (!d_states || (reinterpret_cast<uintptr_t>(d_states) & 15u)) return SV_ERR_INVALID_ARGUMENT;
     if (b->device < 0) {
         if (cudaGetDevice(&b->device) != cudaSuccess ||
             cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)

@@ -177,3 +177,31 @@ def test_gate_launches_replay_from_a_cuda_graph(svmod):
         assert torch.equal(psi, direct)
         s.close()
         d.close()
+
+
+@pytest.mark.gpu
+def test_empty_programs(svmod):
+    """A batch of no states launches nothing (an empty state buffer is
+    accepted); states without gates stay |0...0>, in shared memory (12 qubits)
+    and tiled through global memory (16 qubits): <Z...Z> = <I> = 1 and any
+    string with an X or a Y gives 0."""
+    import torch
+    sv = svmod
+    b = sv.Batch(torch.cuda.current_stream())
+    info = b.compile([], 2)
+    assert info["items"] == 0 and info["state_amps"] == 0
+    b.launch(torch.empty(0, dtype=torch.complex64, device="cuda"))
+    assert b.results() == []
+    states = []
+    for n in (12, 16):
+        p = np.zeros((4, n), np.int32)
+        p[0, :] = 3
+        p[2, 0] = 1
+        p[3, :2] = [2, 3]
+        states.append((n, [], p))
+    b.compile(states, 2)
+    buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
+    b.launch(buf)
+    for got in b.results():
+        assert np.allclose(got, [1.0, 1.0, 0.0, 0.0], atol=1e-12), got
+    b.close()

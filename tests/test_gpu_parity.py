@@ -376,3 +376,22 @@ def test_async_host_copies_round_trip(env):
     sv.sv_copy_to_host(s.handle, sync_out.ctypes.data)
     assert np.array_equal(sync_out, h_out.numpy())
     s.close()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_empty_inputs_launch_nothing(env, name):
+    """No gates, no strings, no samples: every call succeeds, launches no
+    kernel and leaves the state as it was."""
+    torch, sv = env
+    n = 9
+    psi, s = make_state(env, n, name, gen.random_state(n, 99))
+    before = psi.clone()
+    l0 = s.launches()
+    s.apply_circuit([])
+    assert s.apply_fused([], 6) == 0
+    if name == "c64":
+        assert s.apply_fused([], 6, sv.SV_PREC_SPLIT_BF16) == 0
+    assert s.expectation_pauli(np.zeros((0, n), np.int32), np.zeros((0, n), np.int32)).shape == (0,)
+    assert len(s.sample(np.zeros(0))) == 0
+    assert s.launches() == l0
+    assert torch.equal(psi, before)
