@@ -168,11 +168,12 @@ bool plain_cx(const QOp &qo) {
            qo.data[1] == cd(1, 0);
 }
 
-// Pairs each plain controlled exchange (CNOT, control value 0 or 1) with an
-// uncontrolled one-qubit dense op on one of its qubits, where the ops between
-// them all commute with one of the two (act on other qubits): the dense op
-// then writes its outputs straight into the exchanged registers. Returns the
-// window's items in a valid order, each {op, exchange or -1}.
+// Pairs each plain controlled exchange (CNOT, control value 0 or 1) with the
+// nearest earlier uncontrolled one-qubit dense op on one of its qubits, where
+// the ops between them leave that op's qubit alone: the dense op moves forward
+// to the exchange and writes its outputs straight into the exchanged
+// registers. Returns the window's items in a valid order, each {op, exchange
+// or -1}.
 std::vector<std::pair<int, int>> pair_exchanges(const std::vector<QOp> &qops, const std::vector<int> &idx) {
     std::vector<std::pair<int, int>> it;
     for (int i : idx) it.push_back({i, -1});
@@ -186,10 +187,6 @@ std::vector<std::pair<int, int>> pair_exchanges(const std::vector<QOp> &qops, co
                 if ((between & o.qmask) == 0) {            // the dense op moves forward to the exchange
                     it[j] = {it[i].first, it[j].first};
                     it.erase(it.begin() + (long)i);
-                    --j;
-                } else if ((between & cx.qmask) == 0) {    // the exchange moves back to the dense op
-                    it[i].second = it[j].first;
-                    it.erase(it.begin() + (long)j);
                     --j;
                 }
                 break;
