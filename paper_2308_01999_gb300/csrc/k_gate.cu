@@ -112,6 +112,35 @@ k_dense(typename CT<R>::T *__restrict__ sv, uint64_t n_units, GroupGeom G, Offs<
     for (int u = 0; u < U; ++u) {
         const uint64_t unit = u0 + (uint64_t)u * kThreads;
         if (unit >= n_units) continue;
+        if constexpr (K >= 3) {
+            // each output row (two in T0 mode) is stored as soon as its sums are formed: only
+            // the inputs stay live, which for k = 4 halves the registers a thread holds and
+            // lets more blocks share an SM (same sums in the same order)
+            constexpr int RW = (MODE == T0) ? 2 : 1;
+#pragma unroll
+            for (int j0 = 0; j0 < D; j0 += RW) {
+                C w[RW][E];
+#pragma unroll
+                for (int jj = 0; jj < RW; ++jj) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        C acc{0, 0};
+#pragma unroll
+                        for (int l = 0; l < D; ++l) cmad(acc, M.m[(j0 + jj) * D + l], v[u][l][e]);
+                        w[jj][e] = acc;
+                    }
+                }
+                if constexpr (MODE == PAIR)
+                    st16(reinterpret_cast<float2 *>(sv) + base[u] + O.o[j0],
+                         make_float4(w[0][0].x, w[0][0].y, w[0][E - 1].x, w[0][E - 1].y));
+                else if constexpr (MODE == T0)
+                    st16(reinterpret_cast<float2 *>(sv) + base[u] + O.o[j0],
+                         make_float4(w[0][0].x, w[0][0].y, w[RW - 1][0].x, w[RW - 1][0].y));
+                else
+                    sv[base[u] + O.o[j0]] = w[0][0];
+            }
+            continue;
+        }
         C w[D][E];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
