@@ -241,22 +241,47 @@ def test_fused_native_matches_unfused_oracle(env, name, width):
     assert_amps(host(psi), ref, name, f"fused w={width}")
 
 
-def test_full_size_28q_first_layer_sampled(env):
-    """The 28-qubit complex64 benchmark circuit, first layer (42 gates), in the
-    launch configuration the benchmark times; every amplitude is compared."""
+def test_full_size_28q_whole_circuit(env):
+    """The 28-qubit complex64 benchmark circuit, all 40 layers (1680 gates), in
+    the launch configuration the benchmark times (one launch per gate), then
+    the benchmark's reductions: every amplitude is compared with the complex128
+    oracle run of the same circuit, and <Z_q>, the eight random Pauli strings
+    (X and Y sites included, so the compensated single-precision pair sums run
+    over 2^27 pairs per string) and the parity probabilities are compared with
+    the oracle both on the oracle's own state (end to end) and on the GPU's
+    final state (the reduction alone)."""
+    orc.set_threads(0)
     n = 28
-    gates = gen.circuit_config1()[:42]
-    ref = orc.run_circuit(gates, n)
+    gates = gen.circuit_config1()
+    assert len(gates) == 1680
     psi, s = make_state(env, n, "c64")
     s.apply_circuit(gates)
+    z_gpu = s.expectation_z_all()
+    paulis, sites = gen.random_pauli_strings(n, 8, gen.rng_for(101))    # the benchmark's strings
+    assert all(any(c in (1, 2) for c in p) for p in paulis)
+    e_gpu = s.expectation_pauli(paulis, sites)
+    pr_gpu = s.measure_probs([0, n - 1])
     got = psi.cpu().numpy()
+    s.close()
+    ref = orc.run_circuit(gates, n)
     err = 0.0
-    for a in range(0, 1 << n, 1 << 24):
-        err = max(err, float(np.max(np.abs(got[a:a + (1 << 24)].astype(np.complex128) - ref[a:a + (1 << 24)]))))
+    chunk = 1 << 24
+    for a in range(0, 1 << n, chunk):
+        err = max(err, float(np.max(np.abs(got[a:a + chunk].astype(np.complex128) - ref[a:a + chunk]))))
+    print(f"[28q] whole circuit: max|d amp| {err:.3e}")
     assert err <= AMP_TOL["c64"], err
-    z = s.expectation_pauli(np.array([[3], [3], [3]], np.int32), np.array([[0], [13], [27]], np.int32))
-    want = [orc.expect_pauli(ref, [3], [q]).real for q in (0, 13, 27)]
-    assert_exp(z, want, "c64", "28q <Z>")
+    zq = (0, 13, n - 1)
+    assert_exp(z_gpu[list(zq)], [orc.expect_pauli(ref, [3], [q]).real for q in zq], "c64", "28q <Z>")
+    want = np.array([orc.expect_pauli(ref, p, q).real for p, q in zip(paulis, sites)])
+    assert_exp(e_gpu, want, "c64", "28q Pauli strings, oracle state")
+    assert_exp(pr_gpu, orc.parity_probs(ref, [0, n - 1]), "c64", "28q parity probabilities")
+    del ref
+    mine = got.astype(np.complex128)
+    del got
+    own = np.array([orc.expect_pauli(mine, p, q).real for p, q in zip(paulis, sites)])
+    print(f"[28q] Pauli strings: max|d| vs oracle state {np.max(np.abs(e_gpu - want)):.3e}, "
+          f"vs the GPU's own state {np.max(np.abs(e_gpu - own)):.3e}")
+    assert_exp(e_gpu, own, "c64", "28q Pauli strings, GPU state")
 
 
 def test_full_size_28q_echo(env):
