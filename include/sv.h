@@ -102,6 +102,15 @@ SV_API sv_status_t sv_set_stream(sv_handle_t h, void *stream);
 /* Point the handle at another state of the same size and dtype. */
 SV_API sv_status_t sv_set_state_pointer(sv_handle_t h, void *d_state);
 
+/* Point the handle at another state of n_qubits qubits and the given dtype
+ * (device memory, 2^n_qubits amplitudes, 16-byte aligned, caller-owned). The
+ * workspace does not depend on the state's size, so a handle can serve states
+ * of any size in turn without allocating: a pool of handles, one per stream,
+ * replaces sv_create / sv_destroy per state (Table I, "Resource management").
+ * Work already enqueued keeps the state it was given. Errors:
+ * INVALID_ARGUMENT as sv_create. */
+SV_API sv_status_t sv_set_state(sv_handle_t h, int n_qubits, sv_dtype_t dtype, void *d_state);
+
 /* psi <- |index> (one amplitude 1, the rest 0). Asynchronous. */
 SV_API sv_status_t sv_set_basis_state(sv_handle_t h, uint64_t index);
 
@@ -196,7 +205,12 @@ SV_API sv_status_t sv_fuse_plan_ex(const sv_gate_t *gates, int n_gates, int n_qu
 /* Pauli-string expectation values (Table I, "Expectation"):
  * out[s] = Re <psi| P_s |psi>, P_s = prod_i paulis[s*n_sites + i] on qubit
  * sites[s*n_sites + i]. Not divided by <psi|psi>. Products are formed in the
- * state's precision and accumulated in FP64. out is host memory of n_strings
+ * state's precision. complex128: accumulated in FP64. complex64: each thread
+ * adds up to 8 terms in FP32, accumulates those partials in FP32 with
+ * compensation (Neumaier), and everything across threads and blocks is
+ * summed in FP64 in a fixed order (bitwise reproducible); the absolute error
+ * stays below about 1.2e-6 <psi|psi> (the terms' magnitudes sum to at most
+ * <psi|psi>) and is typically far smaller. out is host memory of n_strings
  * doubles. Synchronises the stream. Errors: INVALID_ARGUMENT for a site outside
  * [0, n), a site repeated within a string, a code outside 0..3. */
 SV_API sv_status_t sv_expectation_pauli(sv_handle_t h, const int *paulis, const int *sites,
@@ -351,6 +365,40 @@ SV_API sv_status_t sv_batch_launch(sv_batch_t b, sv_dtype_t dtype, void *d_state
 /* Wait for the last launch and copy its expectation values (FP64, indexed by
  * out_begin + s) to host memory `out` of at least n_out doubles. */
 SV_API sv_status_t sv_batch_results(sv_batch_t b, double *out, int n_out);
+
+/* ---- State memory pool ----
+ * A buddy allocator of state vectors inside one arena of device memory that
+ * the caller allocated once and owns (Sec. II-A, relaxed memory model: the
+ * library does not allocate state memory). A state of n qubits takes a block
+ * of 2^n amplitudes, a power of two of bytes, so blocks are powers of two
+ * aligned to their size and freeing merges buddies. Pure host bookkeeping:
+ * no call touches the arena or calls CUDA; calls are thread-safe. A serving
+ * loop admits a request when sv_pool_alloc finds its block (fragmentation
+ * included) and returns the block when the request finishes, so no device
+ * allocation happens per request. */
+typedef struct sv_pool_ctx *sv_pool_t;
+
+/* Pool over [d_base, d_base + bytes). d_base 256-byte aligned; min_block_bytes
+ * a power of two >= 256 (smaller requests are rounded up to it). An arena that
+ * is not a power of two is cut into maximal aligned power-of-two roots; bytes
+ * beyond the last whole min block are not used. Errors: INVALID_ARGUMENT,
+ * ALLOC (host memory). */
+SV_API sv_status_t sv_pool_create(void *d_base, uint64_t bytes, uint64_t min_block_bytes, sv_pool_t *out);
+SV_API sv_status_t sv_pool_destroy(sv_pool_t p);
+
+/* *d_out = the lowest-addressed free block of the smallest power of two >=
+ * bytes (and >= the minimum block). INSUFFICIENT_WORKSPACE when no free block
+ * is large enough (nothing changes). */
+SV_API sv_status_t sv_pool_alloc(sv_pool_t p, uint64_t bytes, void **d_out);
+
+/* Return a block obtained from sv_pool_alloc. INVALID_ARGUMENT for a pointer
+ * that is not an allocated block of this pool (nothing changes). */
+SV_API sv_status_t sv_pool_free(sv_pool_t p, void *d_ptr);
+
+/* Bytes in allocated blocks, the largest free block, and the usable capacity
+ * (any pointer may be NULL). */
+SV_API sv_status_t sv_pool_stats(sv_pool_t p, uint64_t *bytes_in_use, uint64_t *largest_free_block,
+                                 uint64_t *capacity);
 
 /* A static description of a status code. */
 SV_API const char *sv_status_string(sv_status_t s);

@@ -21,7 +21,7 @@ OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsv.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["sv_api.cu", "sv_fuse.cpp", "k_gate.cu", "k_reduce.cu", "k_tc.cu", "sv_noalloc.cu", "sv_batch.cu", "k_batch.cu"]
+SOURCES = ["sv_api.cu", "sv_fuse.cpp", "k_gate.cu", "k_reduce.cu", "k_tc.cu", "sv_noalloc.cu", "sv_batch.cu", "k_batch.cu", "sv_pool.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", INCLUDE, "-I", CSRC]

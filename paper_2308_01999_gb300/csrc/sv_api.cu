@@ -364,6 +364,16 @@ sv_status_t sv_set_state_pointer(sv_handle_t h, void *d_state) {
     return SV_OK;
 }
 
+sv_status_t sv_set_state(sv_handle_t h, int n_qubits, sv_dtype_t dtype, void *d_state) {
+    if (!h || !d_state || n_qubits < 1 || n_qubits > SV_MAX_QUBITS || (dtype != SV_C64 && dtype != SV_C128) ||
+        (reinterpret_cast<uintptr_t>(d_state) & 15u))
+        return SV_ERR_INVALID_ARGUMENT;
+    h->n = n_qubits;
+    h->dt = dtype;
+    h->sv = d_state;
+    return SV_OK;
+}
+
 sv_status_t sv_set_basis_state(sv_handle_t h, uint64_t index) {
     if (!h || index >= (1ull << h->n)) return SV_ERR_INVALID_ARGUMENT;
     DeviceGuard dg(h->device);

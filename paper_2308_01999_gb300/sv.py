@@ -17,7 +17,7 @@ from dataclasses import dataclass
 import numpy as np
 
 __all__ = [
-    "SvError", "lib", "sv_create", "sv_destroy", "sv_set_stream", "sv_set_state_pointer",
+    "SvError", "lib", "sv_create", "sv_destroy", "sv_set_stream", "sv_set_state_pointer", "sv_set_state",
     "sv_set_basis_state", "sv_copy_from_host", "sv_copy_to_host", "sv_copy_from_host_async",
     "sv_copy_to_host_async", "sv_apply_matrix",
     "sv_apply_fused", "sv_fuse_plan", "sv_expectation_pauli", "sv_measure_probs", "sv_collapse",
@@ -43,7 +43,8 @@ EXPORTED = [
     "sv_batch_create", "sv_batch_destroy", "sv_batch_compile", "sv_batch_info", "sv_batch_launch",
     "sv_batch_results", "sv_swap_index_bits", "sv_apply_pauli_rotation", "sv_sample",
     "sv_check_bounded_wait", "sv_apply_fused_ex", "sv_fuse_plan_ex", "sv_copy_from_host_async",
-    "sv_copy_to_host_async", "sv_batch_compile_ex",
+    "sv_copy_to_host_async", "sv_batch_compile_ex", "sv_set_state", "sv_pool_create", "sv_pool_destroy",
+    "sv_pool_alloc", "sv_pool_free", "sv_pool_stats",
 ]
 
 
@@ -78,7 +79,7 @@ def lib():
         sig = {
             "sv_create": [C.c_int, C.c_int, _VP, _VP, C.POINTER(_VP)],
             "sv_destroy": [_VP], "sv_set_stream": [_VP, _VP], "sv_set_state_pointer": [_VP, _VP],
-            "sv_set_basis_state": [_VP, C.c_uint64],
+            "sv_set_state": [_VP, C.c_int, C.c_int, _VP], "sv_set_basis_state": [_VP, C.c_uint64],
             "sv_copy_from_host": [_VP, _VP], "sv_copy_to_host": [_VP, _VP],
             "sv_copy_from_host_async": [_VP, _VP], "sv_copy_to_host_async": [_VP, _VP],
             "sv_apply_matrix": [_VP, _I, C.c_int, _I, _I, C.c_int, _D, C.c_int],
@@ -101,6 +102,9 @@ def lib():
             "sv_apply_pauli_rotation": [_VP, C.c_double, _I, _I, C.c_int],
             "sv_sample": [_VP, _D, C.c_int, C.POINTER(C.c_int64)],
             "sv_check_bounded_wait": [_VP, C.c_longlong],
+            "sv_pool_create": [_VP, C.c_uint64, C.c_uint64, C.POINTER(_VP)], "sv_pool_destroy": [_VP],
+            "sv_pool_alloc": [_VP, C.c_uint64, C.POINTER(_VP)], "sv_pool_free": [_VP, _VP],
+            "sv_pool_stats": [_VP, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
             "sv_apply_fused_ex": [_VP, C.POINTER(sv_gate_t), C.c_int, C.POINTER(sv_fusion_options_t), _I],
             "sv_fuse_plan_ex": [C.POINTER(sv_gate_t), C.c_int, C.c_int, C.POINTER(sv_fusion_options_t), C.c_int, _I,
                                 _I, _I, _D],
@@ -153,6 +157,10 @@ def sv_set_stream(h: int, stream_ptr: int):
 
 def sv_set_state_pointer(h: int, d_state_ptr: int):
     _check(lib().sv_set_state_pointer(_VP(h), _VP(d_state_ptr)), "sv_set_state_pointer")
+
+
+def sv_set_state(h: int, n_qubits: int, dtype: int, d_state_ptr: int):
+    _check(lib().sv_set_state(_VP(h), int(n_qubits), int(dtype), _VP(d_state_ptr)), "sv_set_state")
 
 
 def sv_set_basis_state(h: int, index: int):
@@ -453,27 +461,35 @@ ITEM_DTYPE = np.dtype([("n_qubits", "<i4"), ("gate_begin", "<i4"), ("n_gates", "
 
 def pack_gates(gates):
     """sv_gate_t records for `gates` (a numpy structured array with the C layout)
-    and the complex128 buffer their matrix pointers point into (keep both alive)."""
+    and the complex128 buffer their matrix pointers point into (keep both alive).
+    Gates are grouped by target and control count so that each group fills its
+    fields with one array assignment."""
     assert C.sizeof(sv_gate_t) == GATE_DTYPE.itemsize
-    sizes = [g.matrix.size for g in gates]
-    buf = np.empty(max(1, sum(sizes)), dtype=np.complex128)
-    rec = np.zeros(len(gates), dtype=GATE_DTYPE)
-    base = buf.ctypes.data
-    off = 0
-    for i, g in enumerate(gates):
-        m = g.matrix.reshape(-1)
-        buf[off:off + m.size] = m
-        r = rec[i]
-        k = len(g.targets)
-        r["n_targets"] = k
-        r["targets"][:k] = g.targets
-        c = len(g.controls)
-        r["n_controls"] = c
-        if c:
-            r["controls"][:c] = g.controls
-            r["control_values"][:c] = g.control_values if g.control_values else (1,) * c
-        r["matrix"] = base + 16 * off
-        off += m.size
+    ng = len(gates)
+    rec = np.zeros(ng, dtype=GATE_DTYPE)
+    if ng == 0:
+        return rec, np.empty(1, dtype=np.complex128)
+    mats = [np.asarray(g.matrix, dtype=np.complex128).reshape(-1) for g in gates]
+    sizes = np.fromiter((m.size for m in mats), dtype=np.int64, count=ng)
+    buf = np.concatenate(mats)
+    offs = np.zeros(ng, dtype=np.int64)
+    np.cumsum(sizes[:-1], out=offs[1:])
+    rec["matrix"] = np.uint64(buf.ctypes.data) + 16 * offs.astype(np.uint64)
+    kt = np.fromiter((len(g.targets) for g in gates), dtype=np.int32, count=ng)
+    kc = np.fromiter((len(g.controls) for g in gates), dtype=np.int32, count=ng)
+    rec["n_targets"] = kt
+    rec["n_controls"] = kc
+    for k in np.unique(kt):
+        idx = np.nonzero(kt == k)[0]
+        rec["targets"][idx, :k] = np.array([gates[i].targets for i in idx], dtype=np.int32).reshape(-1, k)
+    for c in np.unique(kc):
+        if c == 0:
+            continue
+        idx = np.nonzero(kc == c)[0]
+        rec["controls"][idx, :c] = np.array([gates[i].controls for i in idx], dtype=np.int32).reshape(-1, c)
+        rec["control_values"][idx, :c] = np.array(
+            [gates[i].control_values if gates[i].control_values else (1,) * c for i in idx],
+            dtype=np.int32).reshape(-1, c)
     return rec, buf
 
 
@@ -528,48 +544,94 @@ def sv_batch_results(b: int, n_out: int) -> np.ndarray:
     return out[:n_out]
 
 
+@dataclass
+class PackedBatch:
+    """A batch's states in the C layout of sv_batch_compile_ex, packed once and
+    compiled as often as needed (the autotuner compiles several options)."""
+    items: np.ndarray
+    gate_rec: np.ndarray
+    matrices: np.ndarray
+    paulis: np.ndarray
+    n_out: int
+    state_amps: int
+    ns: list
+    gate_counts: list
+
+    @property
+    def offsets(self):
+        return [(int(it["state_offset"]), int(it["n_qubits"]), int(it["out_begin"]), int(it["n_strings"]))
+                for it in self.items]
+
+
+def pack_batch(states, state_offsets=None) -> PackedBatch:
+    """states: list of (n_qubits, gates, paulis) with paulis an (S, n_qubits) int
+    array of Pauli codes. state_offsets (amplitudes, optional): where each state
+    lives relative to the d_states pointer given at launch; by default the
+    states are laid out back to back."""
+    items = np.zeros(len(states), dtype=ITEM_DTYPE)
+    all_gates, pls = [], []
+    g0 = p0 = o0 = 0
+    a0 = 0
+    amps = 0
+    for i, (n, gates, paulis) in enumerate(states):
+        paulis = np.asarray(paulis, dtype=np.int32).reshape(-1, n) if len(paulis) else np.zeros((0, n), np.int32)
+        off = a0 if state_offsets is None else int(state_offsets[i])
+        items[i] = (n, g0, len(gates), p0, paulis.shape[0], o0, off)
+        all_gates.extend(gates)
+        pls.append(paulis.reshape(-1))
+        g0 += len(gates)
+        p0 += paulis.size
+        o0 += paulis.shape[0]
+        a0 += 1 << n
+        amps = max(amps, off + (1 << n))
+    rec, buf = pack_gates(all_gates)
+    pl = np.concatenate(pls) if pls else np.zeros(0, np.int32)
+    return PackedBatch(items, rec, buf, pl, o0, amps, [int(n) for n, _, _ in states],
+                       [len(g) for _, g, _ in states])
+
+
 class Batch:
     """Many independent small circuits (from |0...0>) advanced in one launch.
 
     states: list of (n_qubits, gates, paulis) with paulis an (S, n_qubits) int
-    array of Pauli codes (column q acts on qubit q). Results come back in input
-    order, S values per state."""
+    array of Pauli codes (column q acts on qubit q), or a PackedBatch. Results
+    come back in input order, S values per state. The engine can be compiled
+    and launched again and again; its device program buffer only grows."""
 
     def __init__(self, stream=None):
         self.stream = stream
         ptr = stream.cuda_stream if stream is not None else 0
         self.handle = sv_batch_create(ptr)
         self._keep = None
+        self.choice = None
 
-    def compile(self, states, fusion_width: int = 2, window_qubits: int = 4):
-        items = np.zeros(len(states), dtype=ITEM_DTYPE)
-        all_gates, pls = [], []
-        g0 = p0 = o0 = 0
-        a0 = 0
-        for i, (n, gates, paulis) in enumerate(states):
-            paulis = np.asarray(paulis, dtype=np.int32).reshape(-1, n) if len(paulis) else np.zeros((0, n), np.int32)
-            items[i] = (n, g0, len(gates), p0, paulis.shape[0], o0, a0)
-            all_gates.extend(gates)
-            pls.append(paulis.reshape(-1))
-            g0 += len(gates)
-            p0 += paulis.size
-            o0 += paulis.shape[0]
-            a0 += 1 << n
-        rec, buf = pack_gates(all_gates)
-        pl = np.concatenate(pls) if pls else np.zeros(0, np.int32)
-        sv_batch_compile_ex(self.handle, items, rec, pl, fusion_width, window_qubits)
-        self._keep = (items, rec, buf, pl)
-        self.n_out = o0
-        self.state_amps = a0
-        self.offsets = [(int(it["state_offset"]), int(it["n_qubits"]), int(it["out_begin"]), int(it["n_strings"]))
-                        for it in items]
+    def compile(self, states, fusion_width: int = 2, window_qubits: int = 4, autotune: bool = False,
+                tuner=None, state_offsets=None):
+        """Compile on the host. With autotune (or a tuner given), the fusion and
+        window widths come from the tuner (``autotune.BatchTuner``), which times
+        its candidates on a sample of these states once per workload signature."""
+        packed = states if isinstance(states, PackedBatch) else pack_batch(states, state_offsets)
+        if autotune or tuner is not None:
+            from .autotune import default_tuner
+            tuner = tuner or default_tuner(self.stream)
+            fusion_width, window_qubits = tuner.choose(packed)
+        sv_batch_compile_ex(self.handle, packed.items, packed.gate_rec, packed.paulis, fusion_width, window_qubits)
+        self._keep = packed
+        self.n_out = packed.n_out
+        self.state_amps = packed.state_amps
+        self.offsets = packed.offsets
+        self.choice = (int(fusion_width), int(window_qubits))
         return self.info()
 
     def info(self):
         return sv_batch_info(self.handle)
 
     def launch(self, d_states, keep_states: bool = False):
-        """d_states: a complex64 CUDA tensor of at least `state_amps` elements."""
+        """d_states: a complex64 CUDA tensor of at least `state_amps` elements, or
+        a device address (int) the caller vouches for."""
+        if isinstance(d_states, int):
+            sv_batch_launch(self.handle, d_states, keep_states)
+            return
         if d_states.numel() < self.state_amps:
             raise ValueError("d_states is too small for this batch")
         sv_batch_launch(self.handle, d_states.data_ptr(), keep_states)
@@ -581,6 +643,69 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             sv_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- state memory pool ----
+
+def sv_pool_create(d_base_ptr: int, nbytes: int, min_block_bytes: int = 256) -> int:
+    p = _VP()
+    _check(lib().sv_pool_create(_VP(d_base_ptr), C.c_uint64(nbytes), C.c_uint64(min_block_bytes), C.byref(p)),
+           "sv_pool_create")
+    return p.value
+
+
+def sv_pool_destroy(p: int):
+    _check(lib().sv_pool_destroy(_VP(p)), "sv_pool_destroy")
+
+
+def sv_pool_alloc(p: int, nbytes: int):
+    """Device address of a block of at least nbytes, or None when none is free."""
+    out = _VP()
+    code = lib().sv_pool_alloc(_VP(p), C.c_uint64(nbytes), C.byref(out))
+    if code == 3:
+        return None
+    _check(code, "sv_pool_alloc")
+    return out.value
+
+
+def sv_pool_free(p: int, d_ptr: int):
+    _check(lib().sv_pool_free(_VP(p), _VP(d_ptr)), "sv_pool_free")
+
+
+def sv_pool_stats(p: int) -> dict:
+    a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    _check(lib().sv_pool_stats(_VP(p), C.byref(a), C.byref(b), C.byref(c)), "sv_pool_stats")
+    return {"in_use": a.value, "largest_free": b.value, "capacity": c.value}
+
+
+class StatePool:
+    """Buddy pool of state vectors in one device arena (``sv_pool_*``). The arena
+    is a caller-owned allocation (a torch tensor here) made once; blocks are
+    device addresses inside it."""
+
+    def __init__(self, arena_ptr: int, nbytes: int, min_block_bytes: int = 256):
+        self.base = int(arena_ptr)
+        self.handle = sv_pool_create(self.base, nbytes, min_block_bytes)
+
+    def alloc(self, nbytes: int):
+        return sv_pool_alloc(self.handle, nbytes)
+
+    def free(self, ptr: int):
+        sv_pool_free(self.handle, ptr)
+
+    def stats(self) -> dict:
+        return sv_pool_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sv_pool_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
