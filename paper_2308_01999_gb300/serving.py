@@ -1,22 +1,29 @@
 """Continuous-batching serving loop for state-vector circuits.
 
 Requests (random circuits of 12-30 qubits) arrive over time. Each is admitted
-when its state vector (2^n x 8 bytes, complex64) fits in the free HBM budget,
-keeps that state resident on the device until it finishes, and returns <Z_q>
-for every qubit (FP64). Admitted work overlaps on the GPU:
+when its state vector (2^n x 8 bytes, complex64) finds a block in the HBM
+arena, keeps that block -- its state stays resident on the device -- until it
+finishes, and returns <Z_q> for every qubit (FP64). Admitted work overlaps on
+the GPU:
 
-* small requests (n <= small_max_qubits) that are admitted while the previous
-  batch runs are gathered into the next batch: one persistent launch of the
-  batched engine (``sv.Batch``) advances all of them;
-* every large request runs on its own CUDA stream (a pool of worker threads,
-  one stream each) as one fused call (``sv_apply_fused``, native precision)
-  followed by its expectation values.
+* small requests (n <= small_max_qubits) are gathered into batches: one
+  persistent launch of the batched engine (``sv.Batch``) advances all the
+  states of a batch, their gate layers applied together. Up to
+  ``batch_slots`` batches are in flight at once, so requests that arrive
+  while a batch runs start in the next free slot instead of waiting for that
+  batch to drain;
+* every large request runs on a worker's CUDA stream as one fused call
+  (``sv_apply_fused``, native precision) followed by its expectation values;
+  several large requests run concurrently on different streams.
 
-So requests that arrive while others are on the GPU are admitted as memory
-and workers free up, and their kernels run concurrently with the ones already
-in flight. A request's result does not depend on what else is in the mix: the
-batched kernel gives every state its own CTA and fixed-order reductions, and a
-large request's kernels touch only its own state.
+Nothing is allocated per request: the executor allocates one arena of device
+memory once and places states in it with the library's buddy pool
+(``sv_pool_*``, so admission asks exactly whether a state fits, fragmentation
+included); each call borrows a pooled resource set -- a stream, a handle
+rebound to the request's state with ``sv_set_state``, and a batched engine
+whose device program buffer is reused. A request's result does not depend on what else is in the
+mix: the batched kernel gives every state its own CTA and fixed-order
+reductions, and a large request's kernels touch only its own state.
 
 The scheduler is host code; every computation runs in libsv.so. The executor
 is pluggable so that the scheduling logic can be exercised without a GPU.
@@ -25,6 +32,7 @@ from __future__ import annotations
 
 import collections
 import concurrent.futures as cf
+import contextlib
 import dataclasses
 import threading
 import time
@@ -77,138 +85,220 @@ def latency_stats(reqs) -> dict:
 
 
 class GpuExecutor:
-    """Runs requests on the GPU through libsv.so."""
+    """Runs requests on the GPU through libsv.so without allocating per request.
 
-    def __init__(self, device: int = 0, fusion_width: int = 4, batch_width: int = 2):
+    hbm_budget bytes of device memory are allocated once as the state arena
+    (a block of 2^n complex64 amplitudes per admitted request, placed by the
+    native buddy pool). Each call borrows a worker resource set -- a CUDA
+    stream, a handle and a batched engine -- from a free list; sets are created
+    only when more calls run at once than ever before, and reused afterwards. The
+    plain engines (``run_plain``, ``run_fused_serial``: one request at a time)
+    use one preallocated buffer of the largest state instead of the arena.
+    The batched engine's fusion and window widths come from the autotuner
+    (``autotune.BatchTuner``) unless given."""
+
+    MIN_BLOCK = 1 << 12
+
+    def __init__(self, hbm_budget: int, device: int = 0, fusion_width: int = 4, batch_widths=None,
+                 tuner=None, plain_max_qubits: int = 30):
         import torch
 
         from . import sv
         self.torch, self.sv = torch, sv
         self.device = torch.device("cuda", device)
         self.fusion_width = fusion_width
-        self.batch_width = batch_width
-        self._local = threading.local()
+        self.batch_widths = batch_widths
+        self.tuner = tuner
+        self.arena = torch.empty(int(hbm_budget), dtype=torch.uint8, device=self.device)
+        self.base = self.arena.data_ptr()
+        self.pool = sv.StatePool(self.base, int(hbm_budget), self.MIN_BLOCK)
+        self.capacity = self.pool.stats()["capacity"]
+        self.plain_max_qubits = plain_max_qubits
+        self._plain_buf = None
+        self._workers = []
+        self._free = []
+        self._lock = threading.Lock()
 
-    def _stream(self):
-        s = getattr(self._local, "stream", None)
-        if s is None:
-            s = self.torch.cuda.Stream(self.device)
-            self._local.stream = s
-        return s
-
+    # ---- state memory ----
     def alloc(self, req: Request):
-        return self.torch.empty(1 << req.n, dtype=self.torch.complex64, device=self.device)
+        """Device address of a block for the request's state, or None if none fits now."""
+        return self.pool.alloc(req.state_bytes)
 
-    def run_large(self, req: Request, state) -> np.ndarray:
+    def free(self, ptr):
+        if ptr is not None:
+            self.pool.free(ptr)
+
+    def bytes_in_use(self) -> int:
+        return self.pool.stats()["in_use"]
+
+    # ---- worker resources: a stream, a handle and a batched engine ----
+    @contextlib.contextmanager
+    def _worker(self):
+        """Borrow a resource set from the free list (created on first need; at
+        most as many exist as calls ever ran at once) and return it afterwards."""
+        with self._lock:
+            w = self._free.pop() if self._free else None
+        if w is None:
+            torch, sv = self.torch, self.sv
+            with torch.cuda.device(self.device):
+                stream = torch.cuda.Stream(self.device)
+                h = sv.sv_create(1, sv.SV_C64, self.base, stream.cuda_stream)
+                w = {"stream": stream, "handle": h, "batch": sv.Batch(stream)}
+            with self._lock:
+                self._workers.append(w)
+        try:
+            yield w
+        finally:
+            with self._lock:
+                self._free.append(w)
+
+    def _z_all(self, h, n):
+        return self.sv.sv_expectation_pauli(h, np.full((n, 1), 3, np.int32), np.arange(n, dtype=np.int32)[:, None])
+
+    def run_large(self, req: Request, ptr) -> np.ndarray:
+        """One fused call on the request's state in the arena, then <Z_q> for all q."""
         torch, sv = self.torch, self.sv
-        stream = self._stream()
-        with torch.cuda.device(self.device), torch.cuda.stream(stream):
-            s = sv.StateVector(state, stream)
-            try:
-                s.set_basis_state(0)
-                s.apply_fused(req.gates(), self.fusion_width, sv.SV_PREC_NATIVE)
-                return s.expectation_z_all()
-            finally:
-                s.close()
+        with self._worker() as w, torch.cuda.device(self.device), torch.cuda.stream(w["stream"]):
+            h = w["handle"]
+            sv.sv_set_state(h, req.n, sv.SV_C64, ptr)
+            sv.sv_set_basis_state(h, 0)
+            sv.sv_apply_fused(h, req.gates(), self.fusion_width, sv.SV_PREC_NATIVE)
+            return self._z_all(h, req.n)
+
+    def run_batch(self, reqs, ptrs) -> list:
+        """One persistent launch over the requests' states, each at its arena block."""
+        torch, sv = self.torch, self.sv
+        with self._worker() as w, torch.cuda.device(self.device), torch.cuda.stream(w["stream"]):
+            items = [(r.n, r.gates(), 3 * np.eye(r.n, dtype=np.int32)) for r in reqs]   # row q: Z on qubit q
+            offsets = [(p - self.base) // 8 for p in ptrs]
+            b = w["batch"]
+            if self.batch_widths is not None:
+                b.compile(items, *self.batch_widths, state_offsets=offsets)
+            else:
+                b.compile(items, state_offsets=offsets, tuner=self.tuner, autotune=self.tuner is None)
+            b.launch(self.base)
+            return [np.asarray(v).copy() for v in b.results()]
+
+    def _plain_state(self, req: Request):
+        if req.n > self.plain_max_qubits:
+            raise ValueError("request larger than the plain engine's buffer")
+        if self._plain_buf is None:
+            self._plain_buf = self.torch.empty(8 << self.plain_max_qubits, dtype=self.torch.uint8,
+                                               device=self.device)
+        return self._plain_buf.data_ptr()
 
     def run_plain(self, req: Request) -> np.ndarray:
-        """The plain engine: one launch per gate, unfused, then the expectations."""
+        """The plain engine: one request at a time, one launch per gate (unfused)."""
         torch, sv = self.torch, self.sv
-        stream = self._stream()
-        with torch.cuda.device(self.device), torch.cuda.stream(stream):
-            state = self.alloc(req)
-            s = sv.StateVector(state, stream)
-            try:
-                s.set_basis_state(0)
-                s.apply_circuit(req.gates())
-                return s.expectation_z_all()
-            finally:
-                s.close()
+        with self._worker() as w, torch.cuda.device(self.device), torch.cuda.stream(w["stream"]):
+            h = w["handle"]
+            sv.sv_set_state(h, req.n, sv.SV_C64, self._plain_state(req))
+            sv.sv_set_basis_state(h, 0)
+            for g in req.gates():
+                sv.sv_apply_matrix(h, g.targets, g.matrix, g.controls, g.control_values or None)
+            return self._z_all(h, req.n)
 
-    def run_batch(self, reqs, states) -> list:
+    def run_fused_serial(self, req: Request) -> np.ndarray:
+        """One request at a time with the same fusion as run_large: separates the
+        gain of fusion from the gain of batching and overlap."""
         torch, sv = self.torch, self.sv
-        stream = self._stream()
-        with torch.cuda.device(self.device), torch.cuda.stream(stream):
-            items = [(r.n, r.gates(), 3 * np.eye(r.n, dtype=np.int32)) for r in reqs]   # row q: Z on qubit q
-            b = sv.Batch(stream)
-            try:
-                b.compile(items, fusion_width=self.batch_width)
-                total = sum(1 << r.n for r in reqs)
-                buf = states if states is not None and states.numel() >= total else \
-                    torch.empty(total, dtype=torch.complex64, device=self.device)
-                b.launch(buf)
-                return [np.asarray(v) for v in b.results()]
-            finally:
-                b.close()
+        with self._worker() as w, torch.cuda.device(self.device), torch.cuda.stream(w["stream"]):
+            h = w["handle"]
+            sv.sv_set_state(h, req.n, sv.SV_C64, self._plain_state(req))
+            sv.sv_set_basis_state(h, 0)
+            sv.sv_apply_fused(h, req.gates(), self.fusion_width, sv.SV_PREC_NATIVE)
+            return self._z_all(h, req.n)
+
+    def close(self):
+        self.torch.cuda.synchronize(self.device)
+        with self._lock:
+            for w in self._workers:
+                w["batch"].close()
+                self.sv.sv_destroy(w["handle"])
+            self._workers.clear()
+        self.pool.close()
 
 
 class ServingEngine:
-    """Admission by free memory, continuous batching of small requests, one
-    stream per large request. ``run(requests)`` replays arrival times in real
-    time and returns the requests with t_admit / t_done / result filled in."""
+    """Admission into the executor's state memory, continuous batching of small
+    requests in up to ``batch_slots`` concurrent batches, one stream per large
+    request. ``run(requests)`` replays arrival times in real time and returns
+    the requests with t_admit / t_done / result filled in."""
 
-    def __init__(self, executor, hbm_budget: int, small_max_qubits: int = 20, large_workers: int = 4,
+    def __init__(self, executor, small_max_qubits: int = 20, large_workers: int = 4, batch_slots: int = 2,
                  clock: Callable[[], float] = time.perf_counter, poll_s: float = 0.0005):
         self.ex = executor
-        self.budget = int(hbm_budget)
         self.small_max = small_max_qubits
         self.workers = large_workers
+        self.batch_slots = batch_slots
         self.clock = clock
         self.poll = poll_s
         self.peak_bytes = 0
-        self.occupancy = []          # (t, bytes in use) samples
+        self.occupancy = []          # (t, bytes of admitted states) samples
+        self.batch_sizes = []
 
     def run(self, requests) -> list:
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending = collections.deque(reqs)
         waiting = collections.deque()
         used = 0
-        small_q = []
-        inflight = {}                # future -> (kind, [requests], bytes)
-        pool = cf.ThreadPoolExecutor(max_workers=self.workers + 1)
-        batch_busy = False
+        small_q = []                 # admitted small requests not yet in a batch: (request, block)
+        inflight = {}                # future -> (kind, [requests], [blocks], bytes)
+        pool = cf.ThreadPoolExecutor(max_workers=self.workers + self.batch_slots)
+        batches = 0
         large_busy = 0
         t0 = self.clock()
         now = lambda: self.clock() - t0  # noqa: E731
+        cap = self.ex.capacity
         try:
             while pending or waiting or small_q or inflight:
                 t = now()
                 while pending and pending[0].arrival <= t:
                     waiting.append(pending.popleft())
-                # admission in arrival order, while the state fits the budget
-                while waiting:
-                    r = waiting[0]
-                    if r.state_bytes > self.budget:
-                        waiting.popleft()
+                # admission in arrival order while blocks are found; small requests
+                # may pass a large one that waits for memory or a worker
+                blocked_large = False
+                for r in list(waiting):
+                    small = r.n <= self.small_max
+                    if r.state_bytes > cap:
+                        waiting.remove(r)
                         r.error = "state larger than the HBM budget"
                         r.t_done = now()
                         continue
-                    if used + r.state_bytes > self.budget:
-                        break
-                    if r.n > self.small_max and large_busy >= self.workers:
-                        break
-                    waiting.popleft()
+                    if blocked_large and not small:
+                        continue
+                    if not small and large_busy >= self.workers:
+                        blocked_large = True
+                        continue
+                    blk = self.ex.alloc(r)
+                    if blk is None:
+                        if small:
+                            break
+                        blocked_large = True
+                        continue
+                    waiting.remove(r)
                     used += r.state_bytes
                     r.t_admit = now()
-                    if r.n <= self.small_max:
-                        small_q.append(r)
+                    if small:
+                        small_q.append((r, blk))
                     else:
-                        st = self.ex.alloc(r)
-                        fut = pool.submit(self.ex.run_large, r, st)
-                        inflight[fut] = ("large", [r], r.state_bytes, st)
+                        fut = pool.submit(self.ex.run_large, r, blk)
+                        inflight[fut] = ("large", [r], [blk], r.state_bytes)
                         large_busy += 1
                 self.peak_bytes = max(self.peak_bytes, used)
                 self.occupancy.append((now(), used))
-                # the next batch takes every small request admitted so far
-                if small_q and not batch_busy:
-                    batch = small_q
+                # a free batch slot takes every small request admitted so far
+                if small_q and batches < self.batch_slots:
+                    rs = [r for r, _ in small_q]
+                    blks = [b for _, b in small_q]
                     small_q = []
-                    fut = pool.submit(self.ex.run_batch, batch, None)
-                    inflight[fut] = ("batch", batch, sum(r.state_bytes for r in batch), None)
-                    batch_busy = True
+                    fut = pool.submit(self.ex.run_batch, rs, blks)
+                    inflight[fut] = ("batch", rs, blks, sum(r.state_bytes for r in rs))
+                    self.batch_sizes.append(len(rs))
+                    batches += 1
                 done = [f for f in inflight if f.done()]
                 for f in done:
-                    kind, rs, nbytes, _st = inflight.pop(f)
+                    kind, rs, blks, nbytes = inflight.pop(f)
                     tdone = now()
                     try:
                         res = f.result()
@@ -222,9 +312,11 @@ class ServingEngine:
                             r.error = f"{type(e).__name__}: {e}"
                     for r in rs:
                         r.t_done = tdone
+                    for b in blks:
+                        self.ex.free(b)
                     used -= nbytes
                     if kind == "batch":
-                        batch_busy = False
+                        batches -= 1
                     else:
                         large_busy -= 1
                 if not done:
