@@ -390,10 +390,16 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
                 mma_commit(smem_u32(&S.empty[s]));
                 mma_commit(smem_u32(&S.acc_full[a]));
             }
-            // drain: every MMA issued above has completed once `done` flips
+            // drain: every MMA issued above has completed once `done` flips; if it
+            // does not within the bound, the failure is recorded like any other wait
             mma_commit(smem_u32(&S.done));
             const long long t0 = clock64();
-            while (!mbar_try(smem_u32(&S.done), 0) && clock64() - t0 < kWaitCycles) {
+            bool drained;
+            while (!(drained = mbar_try(smem_u32(&S.done), 0)) && clock64() - t0 < kWaitCycles) {
+            }
+            if (!drained) {
+                *abort_flag = 1;
+                atomicExch(d_err, kErrTimeout);
             }
         }
         __syncwarp();
@@ -724,7 +730,12 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
             }
             mma_commit(smem_u32(&S.done));
             const long long t0 = clock64();
-            while (!mbar_try(smem_u32(&S.done), 0) && clock64() - t0 < kWaitCycles) {
+            bool drained;
+            while (!(drained = mbar_try(smem_u32(&S.done), 0)) && clock64() - t0 < kWaitCycles) {
+            }
+            if (!drained) {
+                *abort_flag = 1;
+                atomicExch(d_err, kErrTimeout);
             }
         }
         __syncwarp();
