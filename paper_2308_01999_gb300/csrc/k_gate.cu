@@ -21,6 +21,7 @@
 // Within a warp, consecutive threads take consecutive units, so for every member
 // the warp reads one contiguous run (coalesced), also for high target qubits.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "sv_internal.h"
@@ -166,6 +167,78 @@ k_dense(typename CT<R>::T *__restrict__ sv, uint64_t n_units, GroupGeom G, Offs<
 #pragma unroll
             for (int j = 0; j < D; ++j) sv[base[u] + O.o[j]] = w[j][0];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// dense, k = 2..4, complex64, qubit 1 a target: warp-staged super-groups
+// ---------------------------------------------------------------------------
+// With qubit 1 a target, consecutive groups (or group pairs) start 32 bytes or
+// more apart, so the thread-per-group access modes above touch only part of
+// every sector per instruction. Here the low bits are taken as a block: with
+// KLO targets below bit B = 5 + KLO, the 2^B amplitudes of bits 0 .. B-1 hold
+// 32 whole groups' low members, contiguous in memory (2^B * 8 >= 512 bytes).
+// A warp takes one super-group -- fixed values of every bit at or above B that
+// is neither a high target nor a control, i.e. 2^(k-KLO) such blocks, one per
+// high member -- loads it with consecutive float4 per lane (every instruction
+// covers whole sectors), writes it to shared memory, lets each lane apply the
+// gate to its own group there, and stores it back the same way. Shared memory
+// is swizzled (amplitude a at a ^ ((a >> 4) & 15), linear over XOR) so that the
+// lanes' group members fall on different banks whatever the target bits.
+template <int KLO> struct LoOffs { uint32_t o[1 << KLO]; uint8_t pos[KLO]; };
+
+__device__ __forceinline__ uint32_t swz(uint32_t a) { return a ^ ((a >> 4) & 15u); }
+
+template <int K, int KLO>
+__global__ void __launch_bounds__(kThreads)
+k_dense_blk(float2 *__restrict__ sv, uint64_t n_sg, GroupGeom Ghi, LoOffs<KLO> Olo, Offs<K - KLO> Ohi,
+            MatK<float, K> M) {
+    constexpr int D = 1 << K, DLO = 1 << KLO;
+    constexpr int B = 5 + KLO, BLK = 1 << B;   // amplitudes of one block: 32 groups' low members
+    constexpr int NA = D * 32;                 // amplitudes of a super-group
+    constexpr int PER = NA / 64;               // float4 per lane
+    __shared__ float2 sm[kThreads / 32][NA];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 *buf = sm[warp];
+    const uint64_t sgi = (uint64_t)blockIdx.x * (kThreads / 32) + warp;
+    if (sgi >= n_sg) return;                   // warp-uniform
+    const uint64_t base = insert_zeros(sgi << B, Ghi);
+    float4 v[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const uint32_t a = 2u * (uint32_t)(lane + 32 * r);
+        v[r] = ld16(sv + base + Ohi.o[a >> B] + (a & (BLK - 1)));
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const uint32_t a = 2u * (uint32_t)(lane + 32 * r), s = swz(a);
+        const float4 f = v[r];
+        *reinterpret_cast<float4 *>(buf + (s & ~1u)) = (s & 1u) ? make_float4(f.z, f.w, f.x, f.y) : f;
+    }
+    __syncwarp();
+    // this lane's group: zero bits inserted at the low target positions
+    uint32_t glo = (uint32_t)lane;
+#pragma unroll
+    for (int i = 0; i < KLO; ++i) {
+        const uint32_t lo = glo & ((1u << Olo.pos[i]) - 1u);
+        glo = ((glo ^ lo) << 1) | lo;
+    }
+    float2 x[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) x[j] = buf[swz((uint32_t)(j >> KLO) * BLK + glo + Olo.o[j & (DLO - 1)])];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < D; ++l) cmad(acc, M.m[j * D + l], x[l]);
+        buf[swz((uint32_t)(j >> KLO) * BLK + glo + Olo.o[j & (DLO - 1)])] = acc;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const uint32_t a = 2u * (uint32_t)(lane + 32 * r), s = swz(a);
+        const float4 f = *reinterpret_cast<const float4 *>(buf + (s & ~1u));
+        st16(sv + base + Ohi.o[a >> B] + (a & (BLK - 1)), (s & 1u) ? make_float4(f.z, f.w, f.x, f.y) : f);
     }
 }
 
@@ -350,6 +423,73 @@ cudaError_t run_dense_reg(const LaunchCtx &L, void *sv, uint64_t n_units, const 
     return cudaGetLastError();
 }
 
+template <int K, int KLO>
+cudaError_t run_dense_blk(const LaunchCtx &L, void *sv, uint64_t n_sg, const GroupGeom &Ghi, const LoOffs<KLO> &Olo,
+                          const Offs<K - KLO> &Ohi, const MatK<float, K> &M) {
+    k_dense_blk<K, KLO><<<grid_for(n_sg, kThreads / 32), kThreads, 0, L.stream>>>(reinterpret_cast<float2 *>(sv), n_sg,
+                                                                                   Ghi, Olo, Ohi, M);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+// The warp-staged kernel takes a dense gate on a complex64 state when qubit 1
+// is a target (k = 4: also when two or more targets fall inside the block),
+// every control sits at or above the block (bit B = 5 + the number of targets
+// below B) and at least one super-group exists. `G` holds
+// the sorted target and control positions; targets ascending in tpos.
+template <int K>
+bool try_dense_blk(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, const MatK<float, K> &M,
+                   cudaError_t &e) {
+    // qubit 1 a target, or (k = 4) two or more targets inside the block: there the
+    // thread-per-group modes leave a warp's accesses spread thin (measured on the
+    // 28-qubit state; a single low target of a 4-qubit gate is faster in PAIR mode)
+    int klo = 0;
+    while (klo < K && tpos[klo] < 5 + klo) ++klo;   // B = 5 + klo with klo targets below B
+    bool t1 = false;
+    for (int t = 0; t < K; ++t) t1 |= tpos[t] == 1;
+    if (!t1 && !(K >= 4 && klo >= 2)) return false;
+    const int B = 5 + klo;
+    GroupGeom Ghi{};
+    Ghi.cset = G.cset;
+    for (int i = 0; i < G.ns; ++i) {
+        if (G.pos[i] < B) {
+            bool is_target = false;
+            for (int t = 0; t < klo; ++t) is_target |= tpos[t] == G.pos[i];
+            if (!is_target) return false;             // a control below the block
+            continue;
+        }
+        Ghi.pos[Ghi.ns++] = G.pos[i];
+    }
+    if (B + Ghi.ns > n) return false;                 // fewer than one super-group
+    const uint64_t n_sg = 1ull << (n - B - Ghi.ns);
+    auto run = [&](auto klo_c) {
+        constexpr int KL = decltype(klo_c)::value;
+        LoOffs<KL> Olo;
+        for (int j = 0; j < (1 << KL); ++j) {
+            uint32_t o = 0;
+            for (int t = 0; t < KL; ++t)
+                if ((j >> t) & 1) o |= 1u << tpos[t];
+            Olo.o[j] = o;
+        }
+        for (int t = 0; t < KL; ++t) Olo.pos[t] = (uint8_t)tpos[t];
+        Offs<K - KL> Ohi;
+        for (int h = 0; h < (1 << (K - KL)); ++h) {
+            uint64_t o = 0;
+            for (int t = 0; t < K - KL; ++t)
+                if ((h >> t) & 1) o |= 1ull << tpos[KL + t];
+            Ohi.o[h] = o;
+        }
+        return run_dense_blk<K, KL>(L, sv, n_sg, Ghi, Olo, Ohi, M);
+    };
+    switch (klo) {
+    case 1: e = run(std::integral_constant<int, 1>{}); break;
+    case 2: e = run(std::integral_constant<int, (K >= 2 ? 2 : 1)>{}); break;
+    case 3: e = run(std::integral_constant<int, (K >= 3 ? 3 : 1)>{}); break;
+    default: e = run(std::integral_constant<int, (K >= 4 ? 4 : 1)>{}); break;
+    }
+    return true;
+}
+
 template <typename R, int K>
 cudaError_t dense_reg(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, const double *mat) {
     using C = typename CT<R>::T;
@@ -366,6 +506,11 @@ cudaError_t dense_reg(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, c
     const uint64_t n_groups = 1ull << (n - G.ns);
     const bool bit0_special = G.ns > 0 && G.pos[0] == 0;
     if constexpr (sizeof(R) == 4) {
+        if constexpr (K >= 2) {
+            // low targets: warp-staged super-groups (needs every control above the block)
+            cudaError_t e;
+            if (try_dense_blk<K>(L, sv, n, G, tpos, M, e)) return e;
+        }
         if (!bit0_special && n_groups >= 2) return run_dense_reg<R, K, PAIR>(L, sv, n_groups / 2, G, O, M);
         if (tpos[0] == 0) return run_dense_reg<R, K, T0>(L, sv, n_groups, G, O, M);
     }

@@ -113,6 +113,33 @@ def test_dense_gates_random_targets_and_controls(env, name, k):
 
 
 @pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("n", [3, 4, 5, 6, 9, 10, 14, 17])
+def test_dense_gates_on_low_target_runs(env, name, n):
+    """Dense 2- to 4-qubit gates with qubit 1 among the targets (staged through
+    shared memory by warps for complex64, when every control lies above the
+    staged block), with and without controls (high and low), targets given in
+    any order, on states from fewer groups than a warp holds to many blocks."""
+    rng = gen.rng_for(300 + n)
+    init = gen.random_state(n, 300 + n)
+    ref = init.copy()
+    psi, s = make_state(env, n, name, init)
+    cases = [(0, 1, 2), (0, 1, 2, 3), (0, 1, 5), (0, 1, 2, 7), (0, 1, 4, 6), (2, 0, 1), (3, 1, 0, 2),
+             (1, 2, 3, 4), (1, 5), (1, 2), (0, 1), (1, 9, 12), (4, 1, 8, 13), (1, 3, 5, 7)]
+    for it, t in enumerate(cases):
+        if max(t) >= n:
+            continue
+        free = [q for q in range(n) if q not in t]
+        c = min(len(free), it % 3, max(0, n - len(t) - 1))
+        ctl = [int(x) for x in rng.choice(free, c, replace=False)] if c else []
+        cv = [int(v) for v in rng.integers(0, 2, size=c)]
+        m = gen.random_gate_dense(rng, len(t))
+        adj = bool(it % 2)
+        s.apply(list(t), m, ctl, cv, adjoint=adj)
+        orc.apply_gate(ref, list(t), m.conj().T if adj else m, ctl, cv)
+    assert_amps(host(psi), ref, name, f"low runs n={n}")
+
+
+@pytest.mark.parametrize("name", NAMES)
 def test_structured_gates(env, name):
     """Diagonal, generalized-permutation and control-revealing dense matrices
     (exercises the structure analysis), incl. bit-0 controls and targets."""
