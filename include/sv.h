@@ -292,16 +292,23 @@ SV_API sv_status_t sv_check_bounded_wait(sv_handle_t h, long long cycles);
 /* Number of kernels this handle has launched since sv_create. */
 SV_API sv_status_t sv_launch_count(sv_handle_t h, uint64_t *out);
 
-/* ---- Batched small state vectors ----
- * Many independent circuits on small states advanced by one persistent launch
- * (gate application and expectation values of Table I, with gate fusion of
+/* ---- Batched state vectors ----
+ * Many independent circuits advanced by one persistent launch (gate
+ * application and expectation values of Table I, with gate fusion of
  * Sec. II-B, on a batch). Each state of up to SV_BATCH_TILE_QUBITS qubits
- * lives in GPU shared memory for its whole circuit; larger ones (up to
- * SV_BATCH_MAX_QUBITS) are processed in passes over 2^14-amplitude tiles that
- * each hold every gate of the pass. States start as |0...0>. complex64 only. */
-#define SV_BATCH_MAX_QUBITS 20
+ * lives in GPU shared memory of one CTA for its whole circuit; larger ones (up
+ * to SV_BATCH_MAX_QUBITS) are processed in passes over 2^14-amplitude tiles
+ * that each hold every gate of the pass, and the tiles of a pass -- and the
+ * chunks of the final expectation sums -- are shared out among all CTAs, so a
+ * large state's gate layers run on the whole GPU together with the other
+ * states' (a CTA waits, with a bounded wait, until the previous pass of that
+ * state has finished). States start as |0...0>. complex64 only. */
+#define SV_BATCH_MAX_QUBITS 26
 #define SV_BATCH_TILE_QUBITS 14
 #define SV_BATCH_KEEP_STATES 1    /* flag: write every final state to d_states */
+#define SV_BATCH_CHECK_WAIT 2     /* flag, diagnostic of device-side failure detection: every wait of the
+                                     launch is for one more pass than the state will ever finish, bounded
+                                     to about 0.1 s; sv_batch_results then returns SV_ERR_TIMEOUT */
 
 typedef struct {
     int n_qubits;           /* 1..SV_BATCH_MAX_QUBITS */
@@ -363,7 +370,12 @@ SV_API sv_status_t sv_batch_info(sv_batch_t b, int *n_items, int *n_stages, int 
 SV_API sv_status_t sv_batch_launch(sv_batch_t b, sv_dtype_t dtype, void *d_states, int flags);
 
 /* Wait for the last launch and copy its expectation values (FP64, indexed by
- * out_begin + s) to host memory `out` of at least n_out doubles. */
+ * out_begin + s) to host memory `out` of at least n_out doubles. Returns
+ * SV_ERR_TIMEOUT if a CTA's bounded wait for another CTA's pass gave up (the
+ * launch then stopped early and its results are not valid). The expectation
+ * sums of a state above SV_BATCH_TILE_QUBITS qubits are formed per chunk of
+ * its amplitudes and added in chunk order, so every value depends only on
+ * that state's circuit and strings, never on the rest of the batch. */
 SV_API sv_status_t sv_batch_results(sv_batch_t b, double *out, int n_out);
 
 /* ---- State memory pool ----

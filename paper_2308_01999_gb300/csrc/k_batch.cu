@@ -379,190 +379,364 @@ __device__ double block_sum(double v, double *red) {
     return t;
 }
 
-__global__ void __launch_bounds__(kT, 1)
-k_batch(float2 *__restrict__ states, const BItem *__restrict__ items, int n_items, const BStage *__restrict__ stages,
-        const BOp *__restrict__ ops, const float2 *__restrict__ pool, const BStr *__restrict__ strs,
-        double *__restrict__ out, int *__restrict__ counter, int keep_states) {
-    extern __shared__ float2 tile[];                 // 2^kBatchTileQubits amplitudes, then the stage's matrices
-    float2 *smat = tile + (1 << kBatchTileQubits);   // kBatchStageMat entries
-    __shared__ float2 msh[2 * 256];                  // one op's matrix when the stage's do not fit
-    __shared__ uint32_t lo_tab[128], hi_tab[128];    // local bits 0..6 / 7..13 -> amplitude bits
-    __shared__ double red[kT / 32];
-    __shared__ int s_item;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int ii = s_item;
-        if (ii >= n_items) break;
-        const BItem it = items[ii];
-        float2 *sv = states + it.state_off;
-        const int n = it.n, T = it.T, L = 1 << T;
-        const uint32_t ntiles = 1u << (n - T);
-        for (int st = it.stage_begin; st < it.stage_end; ++st) {
-            const BStage S = stages[st];
+// Shared state of one CTA (besides the dynamic tile and stage-matrix area).
+struct BSmem {
+    float2 msh[2 * 256];                 // one op's matrix when the stage's do not fit
+    uint32_t lo_tab[128], hi_tab[128];   // local bits 0..6 / 7..13 -> amplitude bits
+    double red[kT / 32];
+    int task;
+    int go;
+};
+
+// Deposit tables of a stage (threads 0..255: local bits 0..6 and 7..13 of a
+// tile index -> amplitude bits) and its matrices in shared memory.
+__device__ bool stage_setup(const BStage &S, int T, const float2 *__restrict__ pool, float2 *smat, BSmem &sh) {
+    if (threadIdx.x < 256) {
+        const int hi = threadIdx.x >> 7, v = threadIdx.x & 127;
+        uint32_t a = 0;
+#pragma unroll
+        for (int b = 0; b < 7; ++b)
+            if (7 * hi + b < T && ((v >> b) & 1)) a |= 1u << S.lpos[7 * hi + b];
+        (hi ? sh.hi_tab : sh.lo_tab)[v] = a;
+    }
+    const bool staged = S.pool_count <= kBatchStageMat;
+    if (staged)
+        for (int i = threadIdx.x; i < S.pool_count; i += kT) smat[i] = pool[S.pool_begin + i];
+    __syncthreads();
+    return staged;
+}
+
+// Every op of a stage on the tile in shared memory.
+__device__ __forceinline__ void stage_ops(float2 *tile, const BStage &S, const BOp *__restrict__ ops, const float2 *__restrict__ pool,
+                          const float2 *smat, bool staged, BSmem &sh, int T) {
+    for (int o = S.op_begin; o < S.op_end; ++o) {
+        const BOp op = ops[o];
+        const float2 *m;
+        if (staged) {
+            m = smat + (op.mat - S.pool_begin);
+            __syncthreads();   // the previous op is done with the tile
+        } else {
+            const int D = 1 << op.k;
+            const int nm = op.kind == BOP_DENSE ? D * D : (op.kind == BOP_PERM ? 2 * D : D);
+            __syncthreads();   // previous op done with the tile and msh
+            for (int i = threadIdx.x; i < nm; i += kT) sh.msh[i] = pool[op.mat + i];
             __syncthreads();
-            if (threadIdx.x < 256) {
-                const int hi = threadIdx.x >> 7, v = threadIdx.x & 127;
-                uint32_t a = 0;
-                int b = 0;
-                for (int q = 0; q < n; ++q) {
-                    if (!((S.lmask >> q) & 1u)) continue;
-                    if (b >= 7 * hi && b < 7 * hi + 7 && ((v >> (b - 7 * hi)) & 1)) a |= 1u << q;
-                    ++b;
-                }
-                (hi ? hi_tab : lo_tab)[v] = a;
+            m = sh.msh;
+        }
+        if (op.kind == BOP_WIN) {
+            // windows only occur in stages whose matrices are staged
+            switch (op.np) {
+            case 2: op_window<2>(tile, op, m, T); break;
+            case 3: op_window<3>(tile, op, m, T); break;
+            default: op_window<4>(tile, op, m, T); break;
             }
-            const uint32_t other = (uint32_t)(~S.lmask & ((1ull << n) - 1ull));
-            // the stage's matrices stay in shared memory for all of its tiles
-            const bool staged = S.pool_count <= kBatchStageMat;
-            if (staged)
-                for (int i = threadIdx.x; i < S.pool_count; i += kT) smat[i] = pool[S.pool_begin + i];
-            __syncthreads();
-            for (uint32_t ti = 0; ti < ntiles; ++ti) {
-                uint32_t tbase = 0;
-                {
-                    uint32_t rem = other, src = ti;
-                    while (rem) {
-                        const uint32_t low = rem & (0u - rem);
-                        if (src & 1u) tbase |= low;
-                        src >>= 1;
-                        rem ^= low;
-                    }
-                }
-                if (st == it.stage_begin) {
-                    for (int l = threadIdx.x; l < L; l += kT)
-                        tile[sw(l)] = make_float2((tbase | lo_tab[l & 127] | hi_tab[l >> 7]) == 0u ? 1.f : 0.f, 0.f);
+        } else if (op.kind == BOP_DENSE) {
+            switch (op.k) {
+            case 1: op_dense<1>(tile, op, m, T); break;
+            case 2: op_dense<2>(tile, op, m, T); break;
+            case 3: op_dense<3>(tile, op, m, T); break;
+            default: op_dense<4>(tile, op, m, T); break;
+            }
+        } else if (op.kind == BOP_PERM) {
+            switch (op.k) {
+            case 1: op_perm<1>(tile, op, m, T); break;
+            case 2: op_perm<2>(tile, op, m, T); break;
+            case 3: op_perm<3>(tile, op, m, T); break;
+            default: op_perm<4>(tile, op, m, T); break;
+            }
+        } else {
+            op_diag(tile, op, m, T);
+        }
+    }
+    __syncthreads();
+}
+
+// Sum over pairs g in [g_lo, g_hi) of one Pauli string's terms, from the tile
+// (in_tile) or from the state in global memory (CG: read at L2, never L1, when
+// other CTAs wrote it). Terms i and i ^ x come from the same pair of loads:
+// w_i = psi_i conj(psi_{i^x}), w_{i^x} = conj(w_i); pairs are enumerated by
+// inserting a zero at the highest bit of x (any set bit would do; the highest
+// keeps a warp's loads contiguous). kU pairs per iteration, all loads issued
+// before any use; the FP32 run of at most 8 terms goes into the FP64 sum after
+// every fourth pair. Returns this thread's FP64 partial.
+template <bool CG>
+__device__ __forceinline__ double pauli_terms(const float2 *tile, const float2 *sv, bool in_tile, const BStr &P,
+                                              uint32_t g_lo, uint32_t g_hi) {
+    const uint32_t x = (uint32_t)P.x, z = (uint32_t)P.z;
+    double acc = 0.0;
+    float run = 0.f;
+    const int pb = x ? 31 - __clz(x) : 0;
+    constexpr int kU = 4;
+    for (uint32_t g0 = g_lo + threadIdx.x; g0 < g_hi; g0 += kU * kT) {
+        float2 a[kU], b[kU];
+        uint32_t ii[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t g = g0 + (uint32_t)u * kT;
+            ii[u] = x ? (((g >> pb) << (pb + 1)) | (g & ((1u << pb) - 1u))) : g;
+            if (g < g_hi) {
+                const uint32_t j = ii[u] ^ x;
+                if constexpr (CG) {
+                    a[u] = __ldcg(sv + ii[u]);
+                    b[u] = x ? __ldcg(sv + j) : a[u];
                 } else {
-                    // eight gathers in flight per thread before the shared-memory writes
-                    for (int l0 = threadIdx.x; l0 < L; l0 += 8 * kT) {
-                        float2 t8[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const int l = l0 + u * kT;
-                            if (l < L) t8[u] = sv[tbase | lo_tab[l & 127] | hi_tab[l >> 7]];
-                        }
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const int l = l0 + u * kT;
-                            if (l < L) tile[sw(l)] = t8[u];
-                        }
-                    }
+                    a[u] = in_tile ? tile[sw(ii[u])] : sv[ii[u]];
+                    b[u] = x ? (in_tile ? tile[sw(j)] : sv[j]) : a[u];
                 }
-                for (int o = S.op_begin; o < S.op_end; ++o) {
-                    const BOp op = ops[o];
-                    const float2 *m;
-                    if (staged) {
-                        m = smat + (op.mat - S.pool_begin);
-                        __syncthreads();   // the previous op is done with the tile
-                    } else {
-                        const int D = 1 << op.k;
-                        const int nm = op.kind == BOP_DENSE ? D * D : (op.kind == BOP_PERM ? 2 * D : D);
-                        __syncthreads();   // previous op done with the tile and msh
-                        for (int i = threadIdx.x; i < nm; i += kT) msh[i] = pool[op.mat + i];
-                        __syncthreads();
-                        m = msh;
-                    }
-                    if (op.kind == BOP_WIN) {
-                        // windows only occur in stages whose matrices are staged
-                        switch (op.np) {
-                        case 2: op_window<2>(tile, op, m, T); break;
-                        case 3: op_window<3>(tile, op, m, T); break;
-                        default: op_window<4>(tile, op, m, T); break;
-                        }
-                    } else if (op.kind == BOP_DENSE) {
-                        switch (op.k) {
-                        case 1: op_dense<1>(tile, op, m, T); break;
-                        case 2: op_dense<2>(tile, op, m, T); break;
-                        case 3: op_dense<3>(tile, op, m, T); break;
-                        default: op_dense<4>(tile, op, m, T); break;
-                        }
-                    } else if (op.kind == BOP_PERM) {
-                        switch (op.k) {
-                        case 1: op_perm<1>(tile, op, m, T); break;
-                        case 2: op_perm<2>(tile, op, m, T); break;
-                        case 3: op_perm<3>(tile, op, m, T); break;
-                        default: op_perm<4>(tile, op, m, T); break;
-                        }
-                    } else {
-                        op_diag(tile, op, m, T);
-                    }
-                }
-                __syncthreads();
-                if (n > T || keep_states)
-                    for (int l = threadIdx.x; l < L; l += kT) sv[tbase | lo_tab[l & 127] | hi_tab[l >> 7]] = tile[sw(l)];
-                __syncthreads();
             }
         }
-        // Pauli expectations: the tile (n == T) or the state in global memory
-        const uint32_t N = 1u << n;
-        for (int s = 0; s < it.n_str; ++s) {
-            const BStr P = strs[it.str_begin + s];
-            const uint32_t x = (uint32_t)P.x, z = (uint32_t)P.z;
-            double acc = 0.0;
-            float run = 0.f;
-            // terms i and i ^ x come from the same pair of loads: w_i = psi_i conj(psi_{i^x}),
-            // w_{i^x} = conj(w_i); pairs are enumerated by inserting a zero at the highest
-            // bit of x (any set bit would do; the highest keeps a warp's loads contiguous)
-            // kU pairs per iteration, all loads issued before any use (memory-level
-            // parallelism for states read from L2 / HBM; kU = 8 spilled registers);
-            // the FP32 run of at most 8 terms goes into the FP64 sum after every
-            // fourth pair
-            const int pb = x ? 31 - __clz(x) : 0;
-            const uint32_t npairs = x ? N / 2 : N;
-            constexpr int kU = 4;
-            for (uint32_t g0 = threadIdx.x; g0 < npairs; g0 += kU * kT) {
-                float2 a[kU], b[kU];
-                uint32_t ii[kU];
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const uint32_t g = g0 + (uint32_t)u * kT;
-                    ii[u] = x ? (((g >> pb) << (pb + 1)) | (g & ((1u << pb) - 1u))) : g;
-                    if (g < npairs) {
-                        const uint32_t j = ii[u] ^ x;
-                        a[u] = n == T ? tile[sw(ii[u])] : sv[ii[u]];
-                        b[u] = x ? (n == T ? tile[sw(j)] : sv[j]) : a[u];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    if (g0 + (uint32_t)u * kT >= npairs) continue;
-                    const uint32_t i = ii[u], j = i ^ x;
-                    const float re = a[u].x * b[u].x + a[u].y * b[u].y, im = a[u].y * b[u].x - a[u].x * b[u].y;
-                    const float ti = P.use_im ? im : re;
-                    run += (__popc(i & z) & 1) ? -ti : ti;
-                    if (x) {
-                        const float tj = P.use_im ? -im : re;
-                        run += (__popc(j & z) & 1) ? -tj : tj;
-                    }
-                    if ((u & 3) == 3) {
-                        acc += (double)run;
-                        run = 0.f;
-                    }
-                }
+        for (int u = 0; u < kU; ++u) {
+            if (g0 + (uint32_t)u * kT >= g_hi) continue;
+            const uint32_t i = ii[u], j = i ^ x;
+            const float re = a[u].x * b[u].x + a[u].y * b[u].y, im = a[u].y * b[u].x - a[u].x * b[u].y;
+            const float ti = P.use_im ? im : re;
+            run += (__popc(i & z) & 1) ? -ti : ti;
+            if (x) {
+                const float tj = P.use_im ? -im : re;
+                run += (__popc(j & z) & 1) ? -tj : tj;
+            }
+            if ((u & 3) == 3) {
                 acc += (double)run;
                 run = 0.f;
             }
-            const double tot = block_sum(acc, red);
-            if (threadIdx.x == 0) out[it.out_begin + s] = (double)P.sign * tot;
         }
+        acc += (double)run;
+        run = 0.f;
+    }
+    return acc;
+}
+
+// Thread 0 waits (bounded) until `need` tile tasks of the item have finished;
+// then every thread may read what they wrote. False when the wait gave up or
+// another CTA had already given up.
+__device__ bool wait_tiles(const BProg &P, int item, unsigned need, BSmem &sh) {
+    if (threadIdx.x == 0) {
+        int go = 1;
+        volatile unsigned *done = P.tiles_done + item;
+        volatile int *status = P.status;
+        const long long t0 = clock64();
+        need += P.need_extra;
+        while (*done < need) {
+            if (*status != 0) {
+                go = 0;
+                break;
+            }
+            if (clock64() - t0 > P.wait_cycles) {
+                atomicExch(P.status, kBatchErrTimeout);
+                go = 0;
+                break;
+            }
+            __nanosleep(256);
+        }
+        __threadfence();
+        sh.go = go;
+    }
+    __syncthreads();
+    return sh.go != 0;
+}
+
+// The tile task is complete: publish its writes, then count it.
+__device__ void finish_tiles(const BProg &P, int item) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(P.tiles_done + item, 1u);
+    }
+}
+
+// Tiles [a, b) of one stage of a state above the tile size.
+__device__ __noinline__ void task_tiles(float2 *tile, float2 *smat, BSmem &sh, float2 *states, const BProg &P,
+                                        const BTask &tk) {
+    const BItem it = P.items[tk.item];
+    float2 *sv = states + it.state_off;
+    const int n = it.n, T = it.T, L = 1 << T;
+    const BStage S = P.stages[tk.stage];
+    const bool staged = stage_setup(S, T, P.pool, smat, sh);
+    const uint32_t other = (uint32_t)(~S.lmask & ((1ull << n) - 1ull));
+    const bool first = tk.stage == it.stage_begin;
+    for (uint32_t ti = tk.a; ti < tk.b; ++ti) {
+        uint32_t tbase = 0;
+        {
+            uint32_t rem = other, src = ti;
+            while (rem) {
+                const uint32_t low = rem & (0u - rem);
+                if (src & 1u) tbase |= low;
+                src >>= 1;
+                rem ^= low;
+            }
+        }
+        __syncthreads();   // the previous tile has been written back
+        if (first) {
+            for (int l = threadIdx.x; l < L; l += kT)
+                tile[sw(l)] = make_float2((tbase | sh.lo_tab[l & 127] | sh.hi_tab[l >> 7]) == 0u ? 1.f : 0.f, 0.f);
+        } else {
+            // eight gathers in flight per thread before the shared-memory writes
+            for (int l0 = threadIdx.x; l0 < L; l0 += 8 * kT) {
+                float2 t8[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int l = l0 + u * kT;
+                    if (l < L) t8[u] = __ldcg(sv + (tbase | sh.lo_tab[l & 127] | sh.hi_tab[l >> 7]));
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int l = l0 + u * kT;
+                    if (l < L) tile[sw(l)] = t8[u];
+                }
+            }
+        }
+        stage_ops(tile, S, P.ops, P.pool, smat, staged, sh, T);
+        for (int l = threadIdx.x; l < L; l += kT) sv[tbase | sh.lo_tab[l & 127] | sh.hi_tab[l >> 7]] = tile[sw(l)];
+    }
+}
+
+// One chunk of the expectation sums of a state above the tile size; the CTA
+// that finishes the state's last chunk adds the partials in chunk order.
+__device__ __noinline__ void task_expect(BSmem &sh, float2 *states, const BProg &P, const BTask &tk) {
+    const BItem it = P.items[tk.item];
+    const float2 *sv = states + it.state_off;
+    const int n = it.n;
+    const uint32_t c = tk.a, nch = (uint32_t)it.n_chunks;
+    for (int s = 0; s < it.n_str; ++s) {
+        const BStr Ps = P.strs[it.str_begin + s];
+        const uint32_t npairs = Ps.x ? (1u << n) / 2 : (1u << n);
+        const uint32_t per = npairs / nch;
+        const double tot = block_sum(pauli_terms<true>(nullptr, sv, false, Ps, c * per, (c + 1) * per), sh.red);
+        if (threadIdx.x == 0) P.parts[it.part_begin + c * it.n_str + s] = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(P.chunks_done + tk.item, 1u);
+        if (prev + 1 == nch) {
+            // every other chunk's partials were published before its count
+            __threadfence();
+            for (int s = 0; s < it.n_str; ++s) {
+                double t = 0.0;
+                for (uint32_t k = 0; k < nch; ++k) t += __ldcg(P.parts + it.part_begin + k * it.n_str + s);
+                P.out[it.out_begin + s] = (double)P.strs[it.str_begin + s].sign * t;
+            }
+        }
+    }
+}
+
+// One state run by one CTA (BT_STATE / BT_WHOLE). A state of T <= 14 qubits
+// lives in the tile for its whole circuit; a larger one is processed stage by
+// stage, each of its 2^(n-T) tiles gathered, updated and written back. Then
+// the expectation values: from the tile (n == T) or, chunk by chunk in the
+// order the split form adds its partials, from the state in global memory.
+__device__ __forceinline__ void run_state(float2 *tile, float2 *smat, BSmem &sh, float2 *states, const BProg &P,
+                                          const BItem &it) {
+    float2 *sv = states + it.state_off;
+    const int n = it.n, T = it.T, L = 1 << T;
+    const uint32_t ntiles = 1u << (n - T);
+    for (int st = it.stage_begin; st < it.stage_end; ++st) {
+        const BStage S = P.stages[st];
+        __syncthreads();
+        const bool staged = stage_setup(S, T, P.pool, smat, sh);
+        const uint32_t other = (uint32_t)(~S.lmask & ((1ull << n) - 1ull));
+        for (uint32_t ti = 0; ti < ntiles; ++ti) {
+            uint32_t tbase = 0;
+            {
+                uint32_t rem = other, src = ti;
+                while (rem) {
+                    const uint32_t low = rem & (0u - rem);
+                    if (src & 1u) tbase |= low;
+                    src >>= 1;
+                    rem ^= low;
+                }
+            }
+            if (st == it.stage_begin) {
+                for (int l = threadIdx.x; l < L; l += kT)
+                    tile[sw(l)] = make_float2((tbase | sh.lo_tab[l & 127] | sh.hi_tab[l >> 7]) == 0u ? 1.f : 0.f, 0.f);
+            } else {
+                // eight gathers in flight per thread before the shared-memory writes
+                for (int l0 = threadIdx.x; l0 < L; l0 += 8 * kT) {
+                    float2 t8[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int l = l0 + u * kT;
+                        if (l < L) t8[u] = sv[tbase | sh.lo_tab[l & 127] | sh.hi_tab[l >> 7]];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int l = l0 + u * kT;
+                        if (l < L) tile[sw(l)] = t8[u];
+                    }
+                }
+            }
+            stage_ops(tile, S, P.ops, P.pool, smat, staged, sh, T);
+            if (n > T || P.keep_states)
+                for (int l = threadIdx.x; l < L; l += kT) sv[tbase | sh.lo_tab[l & 127] | sh.hi_tab[l >> 7]] = tile[sw(l)];
+            __syncthreads();
+        }
+    }
+    const uint32_t nch = n == T ? 1u : (uint32_t)it.n_chunks;
+    for (int s = 0; s < it.n_str; ++s) {
+        const BStr Ps = P.strs[it.str_begin + s];
+        const uint32_t npairs = Ps.x ? (1u << n) / 2 : (1u << n);
+        const uint32_t per = npairs / nch;
+        double t = 0.0;
+        for (uint32_t c = 0; c < nch; ++c) {
+            t += block_sum(pauli_terms<false>(tile, sv, n == T, Ps, c * per, (c + 1) * per), sh.red);
+        }
+        if (threadIdx.x == 0) P.out[it.out_begin + s] = (double)Ps.sign * t;
+    }
+}
+
+// SPLIT = false: every task is a one-CTA state (the program has no split
+// states), so the work list is just the states, largest first. SPLIT = true:
+// the full work list with split states' tile and expectation tasks.
+template <bool SPLIT>
+__global__ void __launch_bounds__(kT, 1) k_batch(float2 *__restrict__ states, const BProg P) {
+    extern __shared__ float2 tile[];                 // 2^kBatchTileQubits amplitudes, then the stage's matrices
+    float2 *smat = tile + (1 << kBatchTileQubits);   // kBatchStageMat entries
+    __shared__ BSmem sh;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if constexpr (SPLIT) sh.task = *(volatile int *)P.status != 0 ? P.n_tasks : atomicAdd(P.counter, 1);
+            else sh.task = atomicAdd(P.counter, 1);
+        }
+        __syncthreads();
+        const int ti_ = sh.task;
+        if (ti_ >= P.n_tasks) break;
+        if constexpr (!SPLIT) {
+            const BItem it = P.items[P.tasks[ti_].item];
+            run_state(tile, smat, sh, states, P, it);
+            continue;
+        }
+        const BTask tk = P.tasks[ti_];
+        if constexpr (SPLIT) {
+            if (tk.kind == BT_TILES) {
+                if (!wait_tiles(P, tk.item, tk.need, sh)) continue;
+                task_tiles(tile, smat, sh, states, P, tk);
+                finish_tiles(P, tk.item);
+                continue;
+            }
+            if (tk.kind == BT_EXPECT) {
+                if (!wait_tiles(P, tk.item, tk.need, sh)) continue;
+                task_expect(sh, states, P, tk);
+                continue;
+            }
+        }
+        const BItem it = P.items[tk.item];
+        run_state(tile, smat, sh, states, P, it);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_batch(const LaunchCtx &L, float2 *states, const BItem *items, int n_items, const BStage *stages,
-                         const BOp *ops, const float2 *pool, const BStr *strs, double *out, int *counter,
-                         int keep_states) {
+cudaError_t launch_batch(const LaunchCtx &L, float2 *states, const BProg &P, bool split) {
     const int smem = (int)sizeof(float2) * ((1 << kBatchTileQubits) + kBatchStageMat);
-    cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(counter, 0, sizeof(int), L.stream);
+    auto kern = split ? k_batch<true> : k_batch<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int grid = L.num_sms;
-    if (grid > n_items) grid = n_items;
+    if (grid > P.n_tasks) grid = P.n_tasks;
     if (grid < 1) grid = 1;
-    k_batch<<<grid, kT, smem, L.stream>>>(states, items, n_items, stages, ops, pool, strs, out, counter, keep_states);
+    kern<<<grid, kT, smem, L.stream>>>(states, P);
     ++*L.launches;
     return cudaGetLastError();
 }

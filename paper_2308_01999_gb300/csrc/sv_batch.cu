@@ -32,6 +32,8 @@ struct sv_batch_ctx {
     std::vector<svk::BOp> ops;
     std::vector<float2> pool;
     std::vector<svk::BStr> strs;
+    std::vector<svk::BTask> tasks;
+    uint32_t n_parts = 0;        // FP64 partial sums of the split states
     int n_out = 0;
     uint64_t state_amps = 0;     // amplitudes the states need in d_states
     bool compiled = false;
@@ -39,7 +41,8 @@ struct sv_batch_ctx {
     char *dbuf = nullptr;
     size_t dbuf_bytes = 0;
     double *d_out = nullptr;
-    int *d_counter = nullptr;
+    int *d_status = nullptr;
+    bool uploaded = false;       // the device copy holds the current program
     uint64_t launches = 0;
 };
 
@@ -352,6 +355,90 @@ SV_API sv_status_t sv_batch_destroy(sv_batch_t b) {
     return SV_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+constexpr uint64_t kBatchTargetTasks = 4096;   // tile tasks aimed at per launch
+constexpr double kBatchCtaShare = 152.0;       // a state holding more than 1/152 of the work is split
+constexpr int kBatchChunkQubits = 17;          // one expectation chunk per 2^17 amplitudes
+
+// The work list of a compiled program (see svk::BTask). A state above the tile
+// size whose work (amplitudes x passes) exceeds one CTA's share of the launch
+// (1/152 of the total, the SM count of the target GPU) is split: each of its
+// stages into tasks of equal tile ranges (a power of two of tiles each), its
+// expectation sums into n_chunks = min(128, 2^max(0, n - 17)) chunks; any
+// other state is one task. Order: stage 0 tasks of every split state, then
+// stage 1 of every split state, ..., then their expectation chunks, then the
+// one-task states, largest first (as items are stored), which fill the tail.
+// A task only waits for tasks earlier in the list.
+void build_tasks(sv_batch_ctx *b) {
+    const int ni = (int)b->items.size();
+    // work of a state: amplitudes times passes (its circuit), the unit of a CTA's share
+    auto work = [](const svk::BItem &it) {
+        return (double)(it.stage_end - it.stage_begin + 1) * (double)(1ull << it.n);
+    };
+    double total = 0.0;
+    for (const svk::BItem &it : b->items) total += work(it);
+    const double share = total / kBatchCtaShare;
+    std::vector<char> split(ni, 0);
+    uint64_t passes = 0;
+    for (int i = 0; i < ni; ++i) {
+        svk::BItem &it = b->items[i];
+        if (it.n <= it.T) continue;
+        split[i] = work(it) > share;
+        if (split[i]) passes += (uint64_t)(it.stage_end - it.stage_begin) << (it.n - it.T);
+        if (it.n_str > 0) {
+            it.n_chunks = 1 << std::min(7, std::max(0, it.n - kBatchChunkQubits));
+            if (split[i]) {
+                it.part_begin = b->n_parts;
+                b->n_parts += (uint32_t)(it.n_chunks * it.n_str);
+            }
+        } else {
+            it.n_chunks = 1;
+        }
+    }
+    // split states: tasks sized so that they number a few thousand, while each
+    // stage of a state is still split in at least min(tiles, 8) tasks
+    uint32_t coarse = 1;
+    while ((uint64_t)coarse * 2 * kBatchTargetTasks <= passes) coarse *= 2;
+    std::vector<uint32_t> per_task(ni, 0), tasks_per_stage(ni, 0);
+    int max_stages = 0;
+    for (int i = 0; i < ni; ++i) {
+        if (!split[i]) continue;
+        const svk::BItem &it = b->items[i];
+        const uint32_t ntiles = 1u << (it.n - it.T);
+        per_task[i] = std::max(1u, std::min(ntiles / 8, coarse));
+        tasks_per_stage[i] = ntiles / per_task[i];
+        max_stages = std::max(max_stages, it.stage_end - it.stage_begin);
+    }
+    for (int sr = 0; sr < max_stages; ++sr)
+        for (int i = 0; i < ni; ++i) {
+            const svk::BItem &it = b->items[i];
+            if (!split[i] || sr >= it.stage_end - it.stage_begin) continue;
+            for (uint32_t k = 0; k < tasks_per_stage[i]; ++k)
+                b->tasks.push_back({svk::BT_TILES, i, it.stage_begin + sr, k * per_task[i], (k + 1) * per_task[i],
+                                    (uint32_t)sr * tasks_per_stage[i], {0, 0}});
+        }
+    for (int i = 0; i < ni; ++i) {
+        if (!split[i]) continue;
+        const svk::BItem &it = b->items[i];
+        const uint32_t all = (uint32_t)(it.stage_end - it.stage_begin) * tasks_per_stage[i];
+        for (int c = 0; c < (it.n_str > 0 ? it.n_chunks : 0); ++c)
+            b->tasks.push_back({svk::BT_EXPECT, i, 0, (uint32_t)c, 0, all, {0, 0}});
+    }
+    // the rest, one CTA each, largest first (items are stored largest first)
+    for (int i = 0; i < ni; ++i) {
+        const svk::BItem &it = b->items[i];
+        if (split[i]) continue;
+        b->tasks.push_back({it.n <= it.T ? svk::BT_STATE : svk::BT_WHOLE, i, 0, 0, 0, 0, {0, 0}});
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
 SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, int n_items, const sv_gate_t *gates,
                                     int n_gates_total, const int *paulis, int fusion_width) {
     const sv_batch_options_t opt{fusion_width, svk::kBatchWinQubits};
@@ -373,6 +460,11 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
     b->ops.clear();
     b->pool.clear();
     b->strs.clear();
+    b->tasks.clear();
+    b->n_parts = 0;
+    b->uploaded = false;
+    b->d_out = nullptr;
+    b->d_status = nullptr;
     b->n_out = 0;
     b->state_amps = 0;
     // largest states first: they take longest, so they start first
@@ -450,6 +542,8 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
             for (int q = 0; q < n && popc64(lm) < T; ++q) lm |= 1ull << q;
             svk::BStage bs{};
             bs.lmask = lm;
+            for (int q = 0, b2 = 0; q < n; ++q)
+                if ((lm >> q) & 1u) bs.lpos[b2++] = (uint8_t)q;
             bs.op_begin = (int)b->ops.size();
             const size_t pool0 = b->pool.size(), ops0 = b->ops.size();
             // windows need the stage's matrices staged in shared memory; if they would
@@ -485,6 +579,7 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
         }
         b->items.push_back(bi);
     }
+    build_tasks(b);
     b->compiled = true;
     return SV_OK;
 }
@@ -510,15 +605,20 @@ SV_API sv_status_t sv_batch_launch(sv_batch_t b, sv_dtype_t dtype, void *d_state
             cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
             return SV_ERR_CUDA;
     }
+    const size_t ni = b->items.size();
     auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t o_items = 0;
-    const size_t o_stages = align(o_items + b->items.size() * sizeof(svk::BItem));
+    const size_t o_stages = align(o_items + ni * sizeof(svk::BItem));
     const size_t o_ops = align(o_stages + b->stages.size() * sizeof(svk::BStage));
     const size_t o_pool = align(o_ops + b->ops.size() * sizeof(svk::BOp));
     const size_t o_strs = align(o_pool + b->pool.size() * sizeof(float2));
-    const size_t o_out = align(o_strs + b->strs.size() * sizeof(svk::BStr));
-    const size_t o_cnt = align(o_out + (size_t)b->n_out * sizeof(double));
-    const size_t total = o_cnt + 256;
+    const size_t o_tasks = align(o_strs + b->strs.size() * sizeof(svk::BStr));
+    const size_t o_out = align(o_tasks + b->tasks.size() * sizeof(svk::BTask));
+    const size_t o_parts = align(o_out + (size_t)b->n_out * sizeof(double));
+    // zeroed at every launch: task counter, status word, per-item counters
+    const size_t o_zero = align(o_parts + (size_t)b->n_parts * sizeof(double));
+    const size_t zero_bytes = 256 + 2 * ni * sizeof(unsigned);
+    const size_t total = o_zero + zero_bytes;
     if (total > b->dbuf_bytes) {
         if (b->dbuf) {
             cudaStreamSynchronize(b->stream);
@@ -531,35 +631,63 @@ SV_API sv_status_t sv_batch_launch(sv_batch_t b, sv_dtype_t dtype, void *d_state
             return SV_ERR_ALLOC;
         }
         b->dbuf_bytes = total;
+        b->uploaded = false;
     }
     auto up = [&](size_t off, const void *src, size_t bytes) {
         return bytes == 0 ? cudaSuccess
                           : cudaMemcpyAsync(b->dbuf + off, src, bytes, cudaMemcpyHostToDevice, b->stream);
     };
-    if (up(o_items, b->items.data(), b->items.size() * sizeof(svk::BItem)) != cudaSuccess ||
-        up(o_stages, b->stages.data(), b->stages.size() * sizeof(svk::BStage)) != cudaSuccess ||
-        up(o_ops, b->ops.data(), b->ops.size() * sizeof(svk::BOp)) != cudaSuccess ||
-        up(o_pool, b->pool.data(), b->pool.size() * sizeof(float2)) != cudaSuccess ||
-        up(o_strs, b->strs.data(), b->strs.size() * sizeof(svk::BStr)) != cudaSuccess)
-        return SV_ERR_CUDA;
+    if (!b->uploaded) {
+        if (up(o_items, b->items.data(), ni * sizeof(svk::BItem)) != cudaSuccess ||
+            up(o_stages, b->stages.data(), b->stages.size() * sizeof(svk::BStage)) != cudaSuccess ||
+            up(o_ops, b->ops.data(), b->ops.size() * sizeof(svk::BOp)) != cudaSuccess ||
+            up(o_pool, b->pool.data(), b->pool.size() * sizeof(float2)) != cudaSuccess ||
+            up(o_strs, b->strs.data(), b->strs.size() * sizeof(svk::BStr)) != cudaSuccess ||
+            up(o_tasks, b->tasks.data(), b->tasks.size() * sizeof(svk::BTask)) != cudaSuccess)
+            return SV_ERR_CUDA;
+        b->uploaded = true;
+    }
+    if (cudaMemsetAsync(b->dbuf + o_zero, 0, zero_bytes, b->stream) != cudaSuccess) return SV_ERR_CUDA;
     b->d_out = reinterpret_cast<double *>(b->dbuf + o_out);
-    b->d_counter = reinterpret_cast<int *>(b->dbuf + o_cnt);
+    b->d_status = reinterpret_cast<int *>(b->dbuf + o_zero + 128);
+    svk::BProg P{};
+    P.items = reinterpret_cast<const svk::BItem *>(b->dbuf + o_items);
+    P.stages = reinterpret_cast<const svk::BStage *>(b->dbuf + o_stages);
+    P.ops = reinterpret_cast<const svk::BOp *>(b->dbuf + o_ops);
+    P.pool = reinterpret_cast<const float2 *>(b->dbuf + o_pool);
+    P.strs = reinterpret_cast<const svk::BStr *>(b->dbuf + o_strs);
+    P.tasks = reinterpret_cast<const svk::BTask *>(b->dbuf + o_tasks);
+    P.n_tasks = (int)b->tasks.size();
+    P.keep_states = (flags & SV_BATCH_KEEP_STATES) ? 1 : 0;
+    P.out = b->d_out;
+    P.parts = reinterpret_cast<double *>(b->dbuf + o_parts);
+    P.counter = reinterpret_cast<int *>(b->dbuf + o_zero);
+    P.status = b->d_status;
+    P.tiles_done = reinterpret_cast<unsigned *>(b->dbuf + o_zero + 256);
+    P.chunks_done = P.tiles_done + ni;
+    P.need_extra = (flags & SV_BATCH_CHECK_WAIT) ? 1u : 0u;
+    P.wait_cycles = (flags & SV_BATCH_CHECK_WAIT) ? 200000000LL : svk::kBatchWaitCycles;
     const svk::LaunchCtx L{b->stream, b->num_sms, &b->launches};
-    cudaError_t e = svk::launch_batch(
-        L, reinterpret_cast<float2 *>(d_states), reinterpret_cast<const svk::BItem *>(b->dbuf + o_items),
-        (int)b->items.size(), reinterpret_cast<const svk::BStage *>(b->dbuf + o_stages),
-        reinterpret_cast<const svk::BOp *>(b->dbuf + o_ops), reinterpret_cast<const float2 *>(b->dbuf + o_pool),
-        reinterpret_cast<const svk::BStr *>(b->dbuf + o_strs), b->d_out, b->d_counter, (flags & 1) ? 1 : 0);
+    bool split = false;
+    for (const svk::BTask &t : b->tasks) split |= t.kind == svk::BT_TILES || t.kind == svk::BT_EXPECT;
+    const cudaError_t e = svk::launch_batch(L, reinterpret_cast<float2 *>(d_states), P, split);
     return e == cudaSuccess ? SV_OK : SV_ERR_CUDA;
 }
 
 SV_API sv_status_t sv_batch_results(sv_batch_t b, double *out, int n_out) {
     if (!b || !b->compiled || (!out && n_out > 0) || n_out < b->n_out) return SV_ERR_INVALID_ARGUMENT;
-    if (b->n_out == 0) return cudaStreamSynchronize(b->stream) == cudaSuccess ? SV_OK : SV_ERR_CUDA;
-    if (!b->d_out) return SV_ERR_INVALID_ARGUMENT;
-    if (cudaMemcpyAsync(out, b->d_out, sizeof(double) * b->n_out, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    if (!b->d_status) {   // nothing launched since the last compile
+        if (b->n_out > 0) return SV_ERR_INVALID_ARGUMENT;
+        return cudaStreamSynchronize(b->stream) == cudaSuccess ? SV_OK : SV_ERR_CUDA;
+    }
+    int status = 0;
+    if (b->n_out > 0 &&
+        cudaMemcpyAsync(out, b->d_out, sizeof(double) * b->n_out, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
         return SV_ERR_CUDA;
-    return cudaStreamSynchronize(b->stream) == cudaSuccess ? SV_OK : SV_ERR_CUDA;
+    if (cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+        return SV_ERR_CUDA;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return SV_ERR_CUDA;
+    return status == 0 ? SV_OK : SV_ERR_TIMEOUT;
 }
 
 }  // extern "C"

@@ -133,13 +133,17 @@ struct BItem {
     int n, T;                // qubits, tile qubits
     int stage_begin, stage_end;
     int str_begin, n_str;    // Pauli strings
-    int out_begin, pad;
+    int out_begin;
+    int n_chunks;            // states above the tile size: expectation chunks
+    uint32_t part_begin;     // their FP64 partial sums: parts[part_begin + chunk * n_str + s]
+    uint32_t pad;
 };
 
 struct BStage {
     uint64_t lmask;          // the T local qubits
     int op_begin, op_end;
     int pool_begin, pool_count;   // the stage's matrices: pool[pool_begin .. pool_begin + pool_count)
+    uint8_t lpos[16];        // the qubit at local position b (b < T), ascending
 };
 constexpr int kBatchStageMat = 4096;   // float2 entries of one stage staged in shared memory at once
 
@@ -158,8 +162,49 @@ struct BStr {
     float sign;              // from i^{nY}
 };
 
-cudaError_t launch_batch(const LaunchCtx &L, float2 *states, const BItem *items, int n_items, const BStage *stages,
-                         const BOp *ops, const float2 *pool, const BStr *strs, double *out, int *counter,
-                         int keep_states);
+// The persistent kernel's work list, taken in order from an atomic counter.
+// A state of at most kBatchTileQubits qubits is one BT_STATE task (its whole
+// circuit in shared memory). A larger state is either one BT_WHOLE task (one
+// CTA runs every pass and the expectation sums, so the state stays warm in L2
+// between its passes) or, when it holds more work than one CTA's share of the
+// launch, split so that many CTAs share it: one BT_TILES task per range of
+// tiles of each stage, and one BT_EXPECT task per chunk of its expectation
+// sums. Both forms add the same per-chunk partial sums in the same order. A task may start only when `need`
+// tile tasks of its state have finished (all of the previous stage, or all
+// stages for BT_EXPECT); every task a task waits for comes earlier in the
+// list, so the earliest unfinished task can always run.
+enum BatchTaskKind { BT_STATE = 0, BT_TILES = 1, BT_EXPECT = 2, BT_WHOLE = 3 };
+struct BTask {
+    int kind, item;
+    int stage;               // BT_TILES: absolute stage index
+    uint32_t a, b;           // BT_TILES: tiles [a, b); BT_EXPECT: chunk a
+    uint32_t need;           // finished tile tasks of the item required first
+    uint32_t pad[2];
+};
+
+// Device pointers of one uploaded program.
+struct BProg {
+    const BItem *items;
+    const BStage *stages;
+    const BOp *ops;
+    const float2 *pool;
+    const BStr *strs;
+    const BTask *tasks;
+    int n_tasks;
+    int keep_states;
+    double *out;             // expectation values
+    double *parts;           // per-chunk partial sums of the split states
+    unsigned *tiles_done;    // per item: finished BT_TILES tasks
+    unsigned *chunks_done;   // per item: finished BT_EXPECT tasks
+    int *counter;            // next task
+    int *status;             // 0, or the timeout code of a wait that gave up
+    unsigned need_extra;     // diagnostic: added to every wait's target (0 in normal runs)
+    long long wait_cycles;   // bound of each wait
+};
+constexpr int kBatchErrTimeout = 0x7c02;
+constexpr long long kBatchWaitCycles = 4000000000LL;   // ~2 s of SM clock per wait
+
+// split: the program holds split states (tile and expectation tasks)
+cudaError_t launch_batch(const LaunchCtx &L, float2 *states, const BProg &P, bool split);
 
 }  // namespace svk

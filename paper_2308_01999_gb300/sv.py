@@ -452,6 +452,7 @@ class StateVector:
 # ---- batched small states ----
 
 SV_BATCH_KEEP_STATES = 1
+SV_BATCH_CHECK_WAIT = 2
 GATE_DTYPE = np.dtype([("n_targets", "<i4"), ("targets", "<i4", (SV_MAX_TARGETS,)), ("n_controls", "<i4"),
                        ("controls", "<i4", (SV_MAX_CONTROLS,)), ("control_values", "<i4", (SV_MAX_CONTROLS,)),
                        ("matrix", "<u8")])
@@ -533,9 +534,9 @@ def sv_batch_info(b: int) -> dict:
             "launches": launches.value}
 
 
-def sv_batch_launch(b: int, d_states_ptr: int, keep_states: bool = False, dtype: int = SV_C64):
-    _check(lib().sv_batch_launch(_VP(b), int(dtype), _VP(d_states_ptr), SV_BATCH_KEEP_STATES if keep_states else 0),
-           "sv_batch_launch")
+def sv_batch_launch(b: int, d_states_ptr: int, keep_states: bool = False, dtype: int = SV_C64, flags: int = 0):
+    flags |= SV_BATCH_KEEP_STATES if keep_states else 0
+    _check(lib().sv_batch_launch(_VP(b), int(dtype), _VP(d_states_ptr), int(flags)), "sv_batch_launch")
 
 
 def sv_batch_results(b: int, n_out: int) -> np.ndarray:
@@ -626,15 +627,15 @@ class Batch:
     def info(self):
         return sv_batch_info(self.handle)
 
-    def launch(self, d_states, keep_states: bool = False):
+    def launch(self, d_states, keep_states: bool = False, flags: int = 0):
         """d_states: a complex64 CUDA tensor of at least `state_amps` elements, or
         a device address (int) the caller vouches for."""
         if isinstance(d_states, int):
-            sv_batch_launch(self.handle, d_states, keep_states)
+            sv_batch_launch(self.handle, d_states, keep_states, flags=flags)
             return
         if d_states.numel() < self.state_amps:
             raise ValueError("d_states is too small for this batch")
-        sv_batch_launch(self.handle, d_states.data_ptr(), keep_states)
+        sv_batch_launch(self.handle, d_states.data_ptr(), keep_states, flags=flags)
 
     def results(self):
         flat = sv_batch_results(self.handle, self.n_out)

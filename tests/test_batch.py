@@ -87,7 +87,7 @@ def test_compile_on_host_only(svmod):
     with pytest.raises(sv.SvError):
         sv.Batch().compile([(3, [gen.Gate((3,), np.eye(2))], np.zeros((0, 3)))], 2)
     with pytest.raises(sv.SvError):
-        sv.Batch().compile([(21, [], np.zeros((0, 21)))], 2)
+        sv.Batch().compile([(27, [], np.zeros((0, 27)))], 2)      # above SV_BATCH_MAX_QUBITS
     with pytest.raises(sv.SvError):
         sv.Batch().compile(states, 5)
     b.close()
@@ -239,4 +239,53 @@ def test_register_window_exchange_cases(svmod, window):
     assert np.max(np.abs(amp - ref)) <= 1e-5
     want = np.array([orc.expect_pauli(ref, p, list(range(n))).real for p in paulis])
     assert np.all(np.abs(res - want) <= 1e-6 * np.maximum(1, np.abs(want)))
+    b.close()
+
+
+@pytest.mark.gpu
+def test_large_states_split_over_the_gpu_match_the_oracle(svmod):
+    """States of 15-24 qubits: every pass of their circuits is split into tile
+    tasks that many CTAs share, and their expectation sums into chunks; next to
+    them, states that fit one CTA. Amplitudes and expectation values against the
+    oracle, in several fusion and window settings."""
+    import torch
+    sv = svmod
+    orc.set_threads(0)
+    sizes = [21, 12, 15, 24, 16, 9, 22]
+    states = _mixed_states(2024, sizes, strings=6)
+    refs = [orc.run_circuit(g, n) for n, g, _ in states]
+    for width, window in ((2, 4), (1, 0), (3, 3)):
+        b = sv.Batch(torch.cuda.current_stream())
+        b.compile(states, fusion_width=width, window_qubits=window)
+        buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
+        b.launch(buf, keep_states=True)
+        res = b.results()
+        host = buf.cpu().numpy()
+        for (n, gates, paulis), (off, _, _, _), got, ref in zip(states, b.offsets, res, refs):
+            amp = host[off:off + (1 << n)].astype(np.complex128)
+            err = np.max(np.abs(amp - ref))
+            assert err <= 1e-5, (n, width, window, err)
+            want = np.array([orc.expect_pauli(ref, p, list(range(n))).real for p in paulis])
+            assert np.all(np.abs(got - want) <= 1e-6 * np.maximum(1, np.abs(want))), (n, got, want)
+        b.close()
+
+
+@pytest.mark.gpu
+def test_results_do_not_depend_on_the_rest_of_the_batch(svmod):
+    """A state's expectation values are bit for bit the same alone and inside a
+    batch of other states, for states that fit one CTA and states split over
+    many (per-chunk partial sums added in a fixed order)."""
+    import torch
+    sv = svmod
+    mix = _mixed_states(99, [18, 11, 20, 14, 16, 13, 19], strings=5)
+    b = sv.Batch(torch.cuda.current_stream())
+    b.compile(mix, fusion_width=2)
+    buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
+    b.launch(buf)
+    together = [r.copy() for r in b.results()]
+    for i in (0, 1, 2, 3):
+        b.compile([mix[i]], fusion_width=2)
+        b.launch(buf)
+        alone = b.results()[0]
+        assert np.array_equal(alone, together[i]), i
     b.close()
