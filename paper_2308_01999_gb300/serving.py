@@ -12,6 +12,10 @@ the GPU:
   ``batch_slots`` batches are in flight at once, so requests that arrive
   while a batch runs start in the next free slot instead of waiting for that
   batch to drain;
+* medium requests (up to batch_max_qubits, at most 26) go to batches of their
+  own: the batched engine splits each of their passes over all CTAs, so
+  resident states of 21-26 qubits also advance together, layer by layer, in
+  one launch;
 * every large request runs on a worker's CUDA stream as one fused call
   (``sv_apply_fused``, native precision) followed by its expectation values;
   several large requests run concurrently on different streams.
@@ -220,15 +224,23 @@ class GpuExecutor:
 
 
 class ServingEngine:
-    """Admission into the executor's state memory, continuous batching of small
-    requests in up to ``batch_slots`` concurrent batches, one stream per large
-    request. ``run(requests)`` replays arrival times in real time and returns
-    the requests with t_admit / t_done / result filled in."""
+    """Admission into the executor's state memory, continuous batching, one
+    stream per large request. Requests of at most ``small_max_qubits`` qubits
+    go to small batches; with ``batch_max_qubits`` above that, requests up to
+    it go to separate medium batches (their states are split over the whole
+    GPU inside the batched launch, so their gate layers run together with the
+    other states'), and only larger ones run as single fused calls. Each batch
+    class has ``batch_slots`` batches in flight at most; a free slot takes every
+    request of its class admitted so far. ``run(requests)`` replays arrival
+    times in real time and returns the requests with t_admit / t_done / result
+    filled in."""
 
     def __init__(self, executor, small_max_qubits: int = 20, large_workers: int = 4, batch_slots: int = 2,
+                 batch_max_qubits: Optional[int] = None,
                  clock: Callable[[], float] = time.perf_counter, poll_s: float = 0.0005):
         self.ex = executor
         self.small_max = small_max_qubits
+        self.batch_max = max(small_max_qubits, batch_max_qubits or small_max_qubits)
         self.workers = large_workers
         self.batch_slots = batch_slots
         self.clock = clock
@@ -237,65 +249,70 @@ class ServingEngine:
         self.occupancy = []          # (t, bytes of admitted states) samples
         self.batch_sizes = []
 
+    def _cls(self, r) -> int:
+        """0: small batch, 1: medium batch, 2: large (single fused call)."""
+        return 0 if r.n <= self.small_max else (1 if r.n <= self.batch_max else 2)
+
     def run(self, requests) -> list:
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending = collections.deque(reqs)
         waiting = collections.deque()
         used = 0
-        small_q = []                 # admitted small requests not yet in a batch: (request, block)
+        queued = ([], [])            # admitted requests of each batch class not yet in a batch: (request, block)
         inflight = {}                # future -> (kind, [requests], [blocks], bytes)
-        pool = cf.ThreadPoolExecutor(max_workers=self.workers + self.batch_slots)
-        batches = 0
+        pool = cf.ThreadPoolExecutor(max_workers=self.workers + 2 * self.batch_slots)
+        batches = [0, 0]
         large_busy = 0
         t0 = self.clock()
         now = lambda: self.clock() - t0  # noqa: E731
         cap = self.ex.capacity
         try:
-            while pending or waiting or small_q or inflight:
+            while pending or waiting or queued[0] or queued[1] or inflight:
                 t = now()
                 while pending and pending[0].arrival <= t:
                     waiting.append(pending.popleft())
-                # admission in arrival order while blocks are found; small requests
+                # admission in arrival order while blocks are found; batched requests
                 # may pass a large one that waits for memory or a worker
                 blocked_large = False
                 for r in list(waiting):
-                    small = r.n <= self.small_max
+                    c = self._cls(r)
                     if r.state_bytes > cap:
                         waiting.remove(r)
                         r.error = "state larger than the HBM budget"
                         r.t_done = now()
                         continue
-                    if blocked_large and not small:
+                    if blocked_large and c == 2:
                         continue
-                    if not small and large_busy >= self.workers:
+                    if c == 2 and large_busy >= self.workers:
                         blocked_large = True
                         continue
                     blk = self.ex.alloc(r)
                     if blk is None:
-                        if small:
+                        if c < 2:
                             break
                         blocked_large = True
                         continue
                     waiting.remove(r)
                     used += r.state_bytes
                     r.t_admit = now()
-                    if small:
-                        small_q.append((r, blk))
+                    if c < 2:
+                        queued[c].append((r, blk))
                     else:
                         fut = pool.submit(self.ex.run_large, r, blk)
                         inflight[fut] = ("large", [r], [blk], r.state_bytes)
                         large_busy += 1
                 self.peak_bytes = max(self.peak_bytes, used)
                 self.occupancy.append((now(), used))
-                # a free batch slot takes every small request admitted so far
-                if small_q and batches < self.batch_slots:
-                    rs = [r for r, _ in small_q]
-                    blks = [b for _, b in small_q]
-                    small_q = []
-                    fut = pool.submit(self.ex.run_batch, rs, blks)
-                    inflight[fut] = ("batch", rs, blks, sum(r.state_bytes for r in rs))
-                    self.batch_sizes.append(len(rs))
-                    batches += 1
+                # a free batch slot of a class takes every request of that class admitted so far
+                for c in (0, 1):
+                    if queued[c] and batches[c] < self.batch_slots:
+                        rs = [r for r, _ in queued[c]]
+                        blks = [b for _, b in queued[c]]
+                        queued[c].clear()
+                        fut = pool.submit(self.ex.run_batch, rs, blks)
+                        inflight[fut] = (c, rs, blks, sum(r.state_bytes for r in rs))
+                        self.batch_sizes.append(len(rs))
+                        batches[c] += 1
                 done = [f for f in inflight if f.done()]
                 for f in done:
                     kind, rs, blks, nbytes = inflight.pop(f)
@@ -315,12 +332,12 @@ class ServingEngine:
                     for b in blks:
                         self.ex.free(b)
                     used -= nbytes
-                    if kind == "batch":
-                        batches -= 1
-                    else:
+                    if kind == "large":
                         large_busy -= 1
+                    else:
+                        batches[kind] -= 1
                 if not done:
-                    if pending and not inflight and not waiting and not small_q:
+                    if pending and not inflight and not waiting and not queued[0] and not queued[1]:
                         time.sleep(max(0.0, min(pending[0].arrival - now(), 0.01)))
                     else:
                         time.sleep(self.poll)

@@ -115,6 +115,20 @@ def test_small_requests_pass_a_large_request_waiting_for_memory():
     assert out[2].t_admit < out[1].t_admit          # the small one did not wait behind the second large one
 
 
+def test_medium_requests_go_to_batches_of_their_own():
+    reqs = serving.make_requests([(0.0, 12, 5, 1), (0.0, 22, 5, 2), (0.001, 13, 5, 3), (0.001, 24, 5, 4),
+                                  (0.002, 28, 5, 5)])
+    ex = FakeExecutor(1 << 34)
+    out = serving.ServingEngine(ex, small_max_qubits=20, batch_max_qubits=26).run(reqs)
+    assert all(r.error is None for r in out)
+    by_rid = {r.rid: r.n for r in out}
+    for b in ex.batches:
+        sizes = [by_rid[i] for i in b]
+        assert all(n <= 20 for n in sizes) or all(20 < n <= 26 for n in sizes), sizes
+    assert any(all(by_rid[i] > 20 for i in b) for b in ex.batches)
+    assert all(by_rid[i] <= 26 for b in ex.batches for i in b)       # the 28-qubit one ran alone
+
+
 def test_serial_engine_orders_and_waits():
     reqs = _trace(8, 400.0)
     out = serving.serial_engine(lambda r: np.zeros(r.n), reqs)
@@ -124,20 +138,21 @@ def test_serial_engine_orders_and_waits():
 
 @pytest.mark.gpu
 def test_results_alone_equal_results_in_the_mix():
-    """Every request of a mixed trace (batched small states and concurrent
-    large ones) gives the same <Z_q> alone and in the mix, and matches the
-    complex128 oracle, for every request size in the trace (12-22 qubits)."""
+    """Every request of a mixed trace (small states batched in shared memory,
+    medium ones batched and split over the GPU, concurrent large ones) gives the
+    same <Z_q> alone and in the mix, and matches the complex128 oracle, for
+    every request size in the trace (12-22 qubits)."""
     import torch
     from oracle import oracle as orc
     orc.set_threads(0)
     ex = serving.GpuExecutor(hbm_budget=8 << 30, fusion_width=4, batch_widths=(2, 4), plain_max_qubits=22)
     trace = gen.serving_trace(count=14, rate=500.0, nmin=12, nmax=22, dmin=3, dmax=8, seed=11)
-    mix = serving.ServingEngine(ex, small_max_qubits=16, large_workers=3, batch_slots=2).run(
-        serving.make_requests(trace))
+    mix = serving.ServingEngine(ex, small_max_qubits=14, batch_max_qubits=18, large_workers=3,
+                                batch_slots=2).run(serving.make_requests(trace))
     assert all(r.error is None for r in mix)
     assert ex.bytes_in_use() == 0
     for r in mix:
-        alone = serving.ServingEngine(ex, small_max_qubits=16, large_workers=3).run(
+        alone = serving.ServingEngine(ex, small_max_qubits=14, batch_max_qubits=18, large_workers=3).run(
             [serving.Request(r.rid, 0.0, r.n, r.depth, r.seed)])[0]
         assert alone.error is None
         assert np.max(np.abs(alone.result - r.result)) <= 1e-6, r.rid
