@@ -557,16 +557,22 @@ def batch_section(args) -> dict:
         t0 = time.perf_counter()
         packed = sv.pack_batch(states)
         out["pack_s"] = round(time.perf_counter() - t0, 2)
-        tuner = autotune.BatchTuner(autotune.gpu_timer(stream), sample=args.tune_sample)
         b = sv.Batch(stream)
         t0 = time.perf_counter()
-        info = b.compile(packed, tuner=tuner)            # the product path: tuned, then compiled
+        if args.batch_widths:
+            # fixed widths, no tuning (profiling captures of one configuration)
+            fw, win = (int(x) for x in args.batch_widths.split(","))
+            info = b.compile(packed, fw, win)
+            out["autotune"] = {"fixed": {"fusion_width": fw, "window_qubits": win}}
+        else:
+            tuner = autotune.BatchTuner(autotune.gpu_timer(stream), sample=args.tune_sample)
+            info = b.compile(packed, tuner=tuner)            # the product path: tuned, then compiled
+            sig = autotune.signature(packed.ns, packed.gate_counts)
+            out["autotune"] = {"sample_states": min(args.tune_sample, len(states)), "signature": list(sig),
+                               "choice": {"fusion_width": b.choice[0], "window_qubits": b.choice[1]},
+                               "sample_ms": {f"fusion{fw}_window{win}": round(t * 1e3, 3)
+                                             for (fw, win), t in tuner.timings[sig].items()}}
         out["tune_and_compile_s"] = round(time.perf_counter() - t0, 2)
-        sig = autotune.signature(packed.ns, packed.gate_counts)
-        out["autotune"] = {"sample_states": min(args.tune_sample, len(states)), "signature": list(sig),
-                           "choice": {"fusion_width": b.choice[0], "window_qubits": b.choice[1]},
-                           "sample_ms": {f"fusion{fw}_window{win}": round(t * 1e3, 3)
-                                         for (fw, win), t in tuner.timings[sig].items()}}
         out["ops"], out["stages"] = info["ops"], info["stages"]
         buf = torch.empty(b.state_amps, dtype=torch.complex64, device=dev)
         for _ in range(2):
@@ -711,33 +717,43 @@ def serve_section(args) -> dict:
         ex.run_fused_serial(r)
     torch.cuda.synchronize()
 
-    def one(rate, count, seed):
-        trace = gen.serving_trace(count=count, rate=rate, seed=seed)
-        eng = serving.ServingEngine(ex, small_max_qubits=20, large_workers=4, batch_slots=2)
+    def served(trace, batch_max):
+        eng = serving.ServingEngine(ex, small_max_qubits=20, batch_max_qubits=batch_max, large_workers=4,
+                                    batch_slots=2)
         mix = eng.run(serving.make_requests(trace))
         occ = eng.occupancy
         tw = 0.0
         for (t_a, b_a), (t_b, _) in zip(occ, occ[1:]):
             tw += b_a * (t_b - t_a)
         span = occ[-1][0] - occ[0][0] if len(occ) > 1 else 1.0
+        rec = {k: round(v, 4) for k, v in serving.latency_stats(mix).items()}
+        rec.update({"hbm_peak_gib": round(eng.peak_bytes / (1 << 30), 2),
+                    "hbm_mean_gib": round(tw / span / (1 << 30), 2), "batches": len(eng.batch_sizes),
+                    "mean_batch_size": round(float(np.mean(eng.batch_sizes)), 2) if eng.batch_sizes else 0})
+        return mix, rec
+
+    def one(rate, count, seed):
+        trace = gen.serving_trace(count=count, rate=rate, seed=seed)
+        mix, rec = served(trace, args.serve_batch_max)
+        alt = 26 if args.serve_batch_max != 26 else 20
+        mix_alt, rec_alt = served(trace, alt)
         plain = serving.serial_engine(ex.run_plain, serving.make_requests(trace))
         fused = serving.serial_engine(ex.run_fused_serial, serving.make_requests(trace))
-        diffs = [float(np.max(np.abs(a.result - b.result))) for a, b in zip(mix, plain)
+        diffs = [float(np.max(np.abs(a.result - b.result))) for m in (mix, mix_alt) for a, b in zip(m, plain)
                  if a.result is not None and b.result is not None]
         service = [r.t_done - r.t_admit for r in plain if r.error is None]
         return {"requests": count, "rate_per_s": round(rate, 3),
-                "served": {k: round(v, 4) for k, v in serving.latency_stats(mix).items()},
+                "served": rec, f"served_batches_to_{alt}_qubits": rec_alt,
                 "plain": {k: round(v, 4) for k, v in serving.latency_stats(plain).items()},
                 "fused_serial": {k: round(v, 4) for k, v in serving.latency_stats(fused).items()},
-                "hbm_peak_gib": round(eng.peak_bytes / (1 << 30), 2),
-                "hbm_mean_gib": round(tw / span / (1 << 30), 2),
-                "batches": len(eng.batch_sizes),
-                "mean_batch_size": round(float(np.mean(eng.batch_sizes)), 2) if eng.batch_sizes else 0,
                 "max_abs_diff_vs_plain": max(diffs) if diffs else None,
                 "plain_capacity_per_s": round(len(service) / sum(service), 3) if service else None}
 
     out = {"workload": "serving trace, Poisson arrivals, qubits 12..30, depth 10..60, complex64, <Z_q> for all q",
            "hbm_budget_gib": round(budget / (1 << 30), 1),
+           "served_config": {"small_batches_to_qubits": 20, "medium_batches_to_qubits": args.serve_batch_max,
+                             "larger": "one fused call each (native, width 4), 4 concurrent streams",
+                             "batch_slots_per_class": 2},
            "batch_widths": {"fusion_width": ex.batch_widths[0], "window_qubits": ex.batch_widths[1]},
            "sample_note": (f"{args.serve_requests} requests of the 10000-request trace at the offered rate: "
                            "the offered load is far above one GPU's capacity, so the trace is a backlog drain "
@@ -752,6 +768,157 @@ def serve_section(args) -> dict:
     del ex
     torch.cuda.empty_cache()
     return out
+
+
+GATE_CASES = ("1:0 1:3 2:0,1 2:3,9 2:1,5 3:0,1,2 3:0,1,5 3:3,9,14 3:20,22,24 3:0,4,9 3:1,9,12 "
+              "4:0,1,2,3 4:0,1,2,7 4:0,1,4,6 4:0,3,6,9 4:1,2,3,4 4:1,3,5,7 4:2,3,4,5 4:3,9,14,20 4:20,22,24,26")
+
+
+def gate_table(args) -> dict:
+    """Dense gates by width and target set: single launches of a random dense
+    2^k x 2^k matrix on a complex64 state, CUDA events around each launch on
+    the handle's stream, L2 flushed (a 256 MiB write) before each, median of
+    five; GB/s counts one read and one write of every amplitude."""
+    import torch
+
+    from paper_2308_01999_gb300 import sv
+
+    n = args.qubits
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    psi = torch.zeros(1 << n, dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    rng = gen.rng_for(5)
+    out = {"n_qubits": n, "state_bytes": 8 << n, "cases": {}}
+    with torch.cuda.stream(stream):
+        s = sv.StateVector(psi, stream)
+        s.set_basis_state(0)
+        for case in args.gate_cases.split():
+            k, ts = case.split(":")
+            t = [int(x) for x in ts.split(",")]
+            assert len(t) == int(k) and max(t) < n
+            m = gen.random_gate_dense(rng, len(t))
+            for _ in range(2):
+                s.apply(t, m)
+            times = []
+            for _ in range(args.gate_reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.apply(t, m)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = float(np.median(times))
+            out["cases"][case] = {"ms": round(ms, 4), "gbs": round(16 * (1 << n) / (ms * 1e-3) / 1e9, 1),
+                                  "fp32_tflops": round(8 * (1 << len(t)) * (1 << n) / (ms * 1e-3) / 1e12, 1)}
+        s.close()
+    return out
+
+
+def run_gate_table(args):
+    print(json.dumps(gate_table(args)))
+
+
+def _oracle_states_worker(args):
+    """One process of the per-state CPU baseline: the oracle, single-threaded,
+    on a slice of the batched workload (ansatz circuit, then the 8 strings)."""
+    lo, hi, count = args
+    from oracle import oracle as orc
+    orc.set_threads(1)
+    work = gen.batched_ansatz_workload(count=count, seed=3)
+    t0 = time.perf_counter()
+    for n, gates, paulis, sites in work[lo:hi]:
+        psi = orc.run_circuit(gates, n)
+        for p_, s_ in zip(paulis, sites):
+            orc.expect_pauli(psi, p_, s_)
+    return time.perf_counter() - t0
+
+
+def cpu_plan(args) -> dict:
+    """The CPU-baseline plan: the oracle as it stands (complex128, plain loops,
+    OpenMP over amplitude groups) timed on this host's cores, with one thread
+    and with all of them, on the 16-qubit parity circuit (whole), the 28-qubit
+    benchmark circuit (all threads: whole; one thread: its first layer) and the
+    4096-state batched workload (all threads: one single-threaded process per
+    core, states dealt round robin; one thread: a stratified sample of 128
+    states, scaled by their share of the total amplitude work). Host memory is
+    reported so that the 64 GiB complex128 run of the 32-qubit brick wall can
+    be judged against it."""
+    import multiprocessing as mp
+
+    from oracle import oracle as orc
+
+    cores = len(os.sched_getaffinity(0))
+    out = {"host_cores": cores, "kind": "oracle"}
+    try:
+        with open("/proc/meminfo") as f:
+            kb = {ln.split(":")[0]: int(ln.split()[1]) for ln in f if ln.split()[0].endswith(":")}
+        out["host_mem_gib"] = round(kb["MemTotal"] / 2**20, 1)
+        out["host_mem_available_gib"] = round(kb.get("MemAvailable", 0) / 2**20, 1)
+    except (OSError, KeyError, ValueError):
+        out["host_mem_gib"] = None
+    out["c128_32q_state_fits_host"] = bool(out.get("host_mem_available_gib") and
+                                           out["host_mem_available_gib"] > 80)
+    # 16-qubit parity circuit
+    gates0 = gen.circuit_config0(0)
+    rec = {}
+    for th in (1, cores):
+        orc.set_threads(th)
+        t0 = time.perf_counter()
+        psi = orc.run_circuit(gates0, 16)
+        orc.expect_z_all(psi)
+        rec[f"threads_{th}_s"] = round(time.perf_counter() - t0, 3)
+    out["circuit16"] = {"gates": len(gates0), **rec}
+    # 28-qubit benchmark circuit
+    gates1 = gen.circuit_config1()
+    orc.set_threads(cores)
+    t0 = time.perf_counter()
+    orc.run_circuit(gates1, 28)
+    dt_all = time.perf_counter() - t0
+    orc.set_threads(1)
+    layer = gates1[:42]
+    t0 = time.perf_counter()
+    orc.run_circuit(layer, 28)
+    dt_one = time.perf_counter() - t0
+    out["circuit28"] = {"gates": len(gates1), f"threads_{cores}_s": round(dt_all, 2),
+                        f"threads_{cores}_gates_per_s": round(len(gates1) / dt_all, 2),
+                        "threads_1_sample": "first layer (42 gates)", "threads_1_sample_s": round(dt_one, 2),
+                        "threads_1_gates_per_s": round(len(layer) / dt_one, 3),
+                        "threads_1_est_s": round(dt_one * len(gates1) / len(layer), 1)}
+    # 4096-state batched workload
+    count = args.batch_states
+    work = gen.batched_ansatz_workload(count=count, seed=3)
+    ns = [n for n, _, _, _ in work]
+    from paper_2308_01999_gb300 import autotune
+    idx = autotune.stratified_sample(ns, 128)
+    orc.set_threads(1)
+    t0 = time.perf_counter()
+    for i in idx:
+        n, gates, paulis, sites = work[i]
+        psi = orc.run_circuit(gates, n)
+        for p_, s_ in zip(paulis, sites):
+            orc.expect_pauli(psi, p_, s_)
+    dt_s = time.perf_counter() - t0
+    share = sum(len(work[i][1]) * (1 << work[i][0]) for i in idx) / sum(len(g) * (1 << n) for n, g, _, _ in work)
+    ctx = mp.get_context("spawn")
+    step = (count + cores - 1) // cores
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_states_worker, [(lo, min(count, lo + step), count) for lo in range(0, count, step)])
+    dt_p = time.perf_counter() - t0
+    out["batch4096"] = {"states": count, f"processes_{cores}_s": round(dt_p, 1),
+                        f"processes_{cores}_states_per_s": round(count / dt_p, 1),
+                        "threads_1_sample": "128 states, stratified by qubit count",
+                        "threads_1_sample_s": round(dt_s, 2),
+                        "threads_1_est_s": round(dt_s / share, 1),
+                        "threads_1_states_per_s": round(count / (dt_s / share), 2)}
+    return out
+
+
+def run_cpu_plan(args):
+    print(json.dumps(cpu_plan(args)))
 
 
 def run_batch(args):
@@ -771,7 +938,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--qubits", type=int, default=28,
                     help="state size; 28 is the benchmark workload, smaller sizes are for profiling captures")
-    ap.add_argument("--workload", choices=("circuit28", "fused32", "batch", "serve"), default="circuit28",
+    ap.add_argument("--workload", choices=("circuit28", "fused32", "batch", "serve", "cpu-plan", "gates"),
+                    default="circuit28",
                     help="fused32: the 32-qubit fused brick-wall study (tensor cores, errors vs complex128)")
     ap.add_argument("--fused-qubits", type=int, default=32)
     ap.add_argument("--no-ref", action="store_true", help="fused32 without the complex128 reference run")
@@ -779,12 +947,17 @@ def main():
     ap.add_argument("--batch-states", type=int, default=4096, help="batch: number of states")
     ap.add_argument("--plain-sample", type=int, default=256, help="batch: states run through the plain engine")
     ap.add_argument("--tune-sample", type=int, default=1024, help="batch: states the autotuner times")
+    ap.add_argument("--batch-widths", default="", help="batch: 'fusion,window' widths instead of the autotuner")
+    ap.add_argument("--gate-cases", default=GATE_CASES, help="gates: 'k:t0,t1,..' cases, space separated")
+    ap.add_argument("--gate-reps", type=int, default=5, help="gates: timed launches per case")
     ap.add_argument("--main-only", action="store_true",
                     help="only the 28-qubit line, without its batch and serve sections")
     ap.add_argument("--serve-requests", type=int, default=120, help="serve: requests of the offered-rate trace")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serve: offered arrival rate (1/s)")
     ap.add_argument("--serve-low-requests", type=int, default=40, help="serve: requests of the 0.7x-capacity trace")
     ap.add_argument("--serve-budget-gb", type=float, default=200.0, help="serve: HBM budget for resident states")
+    ap.add_argument("--serve-batch-max", type=int, default=20,
+                    help="serve: largest request (qubits) that goes to a batch; larger ones run as fused calls")
     ap.add_argument("--precs", default="tf32,bf16,native", help="fused32: precisions")
     args = ap.parse_args()
     global N_QUBITS
@@ -797,6 +970,10 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "cpu-plan":
+        run_cpu_plan(args)
+    elif args.workload == "gates":
+        run_gate_table(args)
     else:
         run_ours(args)
 
