@@ -6,10 +6,11 @@
 // View the state as 64 x 2^(n-6): column c holds the 64 members of group c (the
 // amplitudes whose non-target bits spell c); one fused gate G is the same
 // product for every column. Two kernels:
-//   k_tc6_raw (qubit 0 not a target, the common case): the state tile itself is
-//     the MN-major B operand and the contraction runs over the 64 members
-//     (described at the kernel);
-//   k_tc6 (qubit 0 a target): with x_c the 128 reals of column c (re, im
+//   k_tc6_raw (every state of 7 qubits or more): the state tile itself is the
+//     MN-major B operand and the contraction runs over the 64 members
+//     (described at the kernel); with qubit 0 a target the tile's member pairs
+//     are rearranged into member rows in shared memory;
+//   k_tc6 (a 6-qubit state, one column): with x_c the 128 reals of column c (re, im
 //     interleaved: K index 2j + e for member j),
 //       out_c = A x_c,  A[2j+e][2l+f] = the real 2x2 block [[Re, -Im], [Im, Re]] of G[j][l],
 //     i.e. the real GEMM D(128 x N) = A(128 x 128) * B(128 x N) with B's
@@ -41,6 +42,8 @@
 // expiry the kernel records an error code in the device status word, drains
 // its own MMAs (again bounded), frees its TMEM and returns.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include <cstring>
 #include <vector>
@@ -453,7 +456,7 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-// ---------------- raw-operand variant (TF32 or split BF16, qubit 0 not a target) ----------------
+// ---------------- raw-operand variant (TF32 or split BF16) ----------------
 // The same product written with the member index as the contraction:
 //   D(128 x 256) = A(128 x 64) * B(64 x 256),  B[l][2i + f] = component f of
 //   amplitude (member l, column i),  A row m = 32q + r: member j = 16q + r % 16,
@@ -476,7 +479,13 @@ k_tc6(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *_
 // one thread issues the MMAs (TF32: 8 of K = 8; BF16: Ahi Bhi + Ahi Blo + Alo Bhi
 // for 4 steps of K = 16); 8 epilogue warps combine, write the tile's result into
 // the stage it came from and store it back in runs of columns. Three stages
-// rotate. Needs qubit 0 free (a chunk is two adjacent amplitudes).
+// rotate. With qubit 0 free a 16-byte chunk is two adjacent amplitudes (columns
+// 2p, 2p + 1) of one member; with qubit 0 a target (T0) it is members 2m, 2m + 1
+// of one column: the copies land columns 2p and 2p + 1 in rows 2m and 2m + 1 of
+// pair p, the convert stage trades the rows' 8-byte halves (TF32: in the same
+// pass as the rounding; BF16: by one shuffle before the split), and the epilogue
+// trades them back (one shuffle between the lanes of rows j and j ^ 1) before
+// the result is stored in memory order.
 constexpr int kNT3 = 128;                     // columns per tile (MMA N = 2 * kNT3 reals)
 constexpr int kStages3 = 3;
 constexpr int kA3 = 128 * 64 * 4;             // A image: 128 rows x 64 tf32 (or BF16 hi + lo), K-major
@@ -488,7 +497,6 @@ constexpr int kEpiWarps3 = 8;                 // warps 6-13
 constexpr int kMmaWarp3 = kProdWarps3 + kEpiWarps3;
 constexpr int kThreads3 = (kMmaWarp3 + 1) * 32;
 constexpr int kTmemCols3 = 2 * 2 * kNT3;      // two accumulators of 256 columns
-constexpr int kRawMinLowTarget = 1;          // lowest target the launcher sends here
 
 struct TcCtl3 {
     unsigned long long landed[kStages3], full[kStages3], empty[kStages3], acc_full[2], acc_empty[2], done;
@@ -533,6 +541,7 @@ __host__ __device__ constexpr uint32_t idesc3() {
 // swizzle with 32-byte atomicity) into hi / lo atoms of 8 rows x 32 BF16 (64-byte
 // swizzle: 16-byte chunk c of row r at r * 64 + ((c ^ (r / 2 % 4)) << 4)) at atom
 // and atom + 512. Every lane reads its 32 bytes before any lane writes.
+template <bool T0 = false>
 __device__ __forceinline__ void split_atom(uint32_t atom, int lane) {
     const int r = lane >> 2, u = lane & 3;          // row, physical 32-byte unit
     const int lu = u ^ (r & 3);                     // logical unit: floats 8 lu .. 8 lu + 7
@@ -543,6 +552,25 @@ __device__ __forceinline__ void split_atom(uint32_t atom, int lane) {
     asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
                  : "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
                  : "r"(atom + (uint32_t)(r * 128 + u * 32 + 16)));
+    if constexpr (T0) {
+        // rows 2m, 2m + 1 landed as member pairs of columns 2p, 2p + 1 (qubit 0 a
+        // target): trade 8-byte halves with the lane holding the same columns of
+        // the other row (lane ^ 5), so each row holds its own member of both columns
+        const bool even = (r & 1) == 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float *c = x + 4 * h;
+            const float s0 = __shfl_xor_sync(0xffffffffu, even ? c[2] : c[0], 5);
+            const float s1 = __shfl_xor_sync(0xffffffffu, even ? c[3] : c[1], 5);
+            if (even) {
+                c[2] = s0;
+                c[3] = s1;
+            } else {
+                c[0] = s0;
+                c[1] = s1;
+            }
+        }
+    }
     uint32_t hi[4], lo[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) split_bf16(x[2 * k], x[2 * k + 1], hi[k], lo[k]);
@@ -561,15 +589,41 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
-// IL (lowest target t0 = 1..3): the amplitude pairs of member l run for
-// g = 2^(t0-1) pairs and are followed by those of member l ^ 1 (member bit 0 is
-// amplitude bit t0), so groups of g lanes alternate between l and l ^ 1 and every
-// copy and store instruction covers one contiguous run; otherwise (t0 >= 4, runs
-// of at least 128 bytes) all lanes of an instruction take one member and
-// consecutive pairs. lg = log2 g.
-template <int P, bool IL>
+// Which chunk of the tile each copy (and store) moves is set by the host
+// (RawMap): with qubit 0 free a chunk is amplitudes (2p, 2p + 1) of member row l
+// (2 x 6 index bits: the member's bits sit at the target positions, the pair's at
+// non-target positions 1..6); with qubit 0 a target (T0) it is members 2m, 2m + 1
+// of one column c (5 member-pair bits at target positions 1..5, 7 column bits at
+// the non-target positions), landed in row 2m + (c & 1) of pair c / 2 and turned
+// into member rows by the convert stage. The index bits are ordered by the
+// address position they set (the three lowest lane bits chosen among the low
+// ones so that eight consecutive lanes hit eight different 16-byte bank groups
+// of shared memory); the five first vary across the lanes of a warp, the next
+// one across the two copy warps, the rest across a thread's copies.
+// Both the amplitude address and the operand offset (mn_chunk is linear over
+// XOR) are OR / XOR of per-bit contributions, so a thread combines one
+// per-thread and one per-copy table entry.
+struct RawMap {
+    uint64_t cthr_addr[64], cit_addr[64];   // copy: amplitude offset, thread part / copy part
+    uint32_t cthr_sm[64], cit_sm[64];       // copy: operand byte offset in a stage
+    uint32_t cthr_col[64], cit_col[64];     // copy: first column of the chunk (ragged tiles)
+    uint64_t sl_addr[32], sr_addr[16];      // store: lane part / iteration part (one epilogue warp)
+    uint32_t sl_sm[32], sr_sm[16];
+    uint32_t sl_col[32], sr_col[16];
+};
+
+// Copy and store orders: PLAIN and IL are fixed orders for qubit 0 free (PLAIN:
+// each instruction 32 consecutive amplitude pairs of one member; IL, lowest
+// target t0 = 1..3: groups of g = 2^(t0-1) lanes alternate between members l and
+// l ^ 1, lg = log2 g), MAPPED the table order of RawMap (qubit 0 free), T0 the
+// table order with qubit 0 a target.
+enum RawMode { RAW_PLAIN = 0, RAW_IL = 1, RAW_MAPPED = 2, RAW_T0 = 3 };
+
+template <int P, int MODE>
 __global__ void __launch_bounds__(kThreads3, 1)
-k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, int *__restrict__ d_err, int lg) {
+k_tc6_raw(float2 *__restrict__ sv, const TcGeom G, const RawMap R, const uint4 *__restrict__ a_img,
+          int *__restrict__ d_err, int lg) {
+    constexpr bool T0 = MODE == RAW_T0, TABLE = MODE == RAW_MAPPED || MODE == RAW_T0, IL = MODE == RAW_IL;
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     if (smem_u32(smem_dyn) & 1023u) {
         if (threadIdx.x == 0) atomicExch(d_err, kErrSmemAlign);
@@ -611,43 +665,67 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
 
     if (warp < kCopyWarps3) {
         // ---------------- copy ----------------
-        // Thread c takes amplitude pair c of all 64 members (a warp load is 32 consecutive
-        // pairs of one member: 512 contiguous bytes once the lowest target is 6 or more);
-        // with IL, thread t takes pairs c' and c' + 32 (c' = t % g + (t / 2g) g) of the
-        // members with bit 0 = (t / g) % 2.
         // The copies signal `landed` themselves (cp.async.mbarrier.arrive), so these
         // threads never wait for data.
         const int tid = threadIdx.x;
-        const int g = 1 << lg;
-        const int c0 = IL ? (tid & (g - 1)) + ((tid >> (lg + 1)) << lg) : tid;
-        const uint64_t pc0 = col_base((uint64_t)(2 * c0), G);
-        const uint64_t pc1 = col_base((uint64_t)(2 * (c0 + 32)), G);
-        const bool ok0 = (uint64_t)(2 * c0) < G.n_cols, ok1 = (uint64_t)(2 * (c0 + 32)) < G.n_cols;
-        const int mb = IL ? (tid >> lg) & 1 : 0;
-        const uint64_t offb = IL ? G.off[mb] : 0;
         int i = 0;
-        for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
-            const int s = i % kStages3, u = i / kStages3;
-            if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
-            const uint64_t tb = col_base(t * kNT3, G);
-            const uint32_t sb = sB0 + (uint32_t)(s * kB3);
-            if constexpr (IL) {
-                const uint64_t b0 = tb | pc0 | offb, b1 = tb | pc1 | offb;
-#pragma unroll 8
-                for (int m = 0; m < 32; ++m) {
-                    const int l = 2 * m + mb;
-                    const uint64_t om = G.off[2 * m];
-                    cp_async16(sb + mn_chunk(l, c0), ok0 ? sv + (b0 | om) : sv, ok0 ? 16u : 0u);
-                    cp_async16(sb + mn_chunk(l, c0 + 32), ok1 ? sv + (b1 | om) : sv, ok1 ? 16u : 0u);
-                }
-            } else {
-                const uint64_t b0 = tb | pc0;
+        if constexpr (TABLE) {
+            // chunk k of thread t is chunk index cthr[t] ^ cit[k] of the tile (RawMap)
+            const uint64_t ta = R.cthr_addr[tid];
+            const uint32_t tsm = R.cthr_sm[tid], tcol = R.cthr_col[tid];
+            const bool full = G.n_cols >= (uint64_t)kNT3;
+            for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+                const int s = i % kStages3, u = i / kStages3;
+                if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
+                const uint64_t tb = col_base(t * kNT3, G) | ta;
+                const uint32_t sb = sB0 + (uint32_t)(s * kB3);
+                if (full) {
 #pragma unroll 16
-                for (int l = 0; l < 64; ++l)
-                    cp_async16(sb + mn_chunk(l, c0), ok0 ? sv + (b0 | G.off[l]) : sv, ok0 ? 16u : 0u);
+                    for (int k = 0; k < 64; ++k) cp_async16(sb + (tsm ^ R.cit_sm[k]), sv + (tb | R.cit_addr[k]), 16u);
+                } else {
+                    for (int k = 0; k < 64; ++k) {
+                        const bool ok = (uint64_t)(tcol | R.cit_col[k]) < G.n_cols;
+                        cp_async16(sb + (tsm ^ R.cit_sm[k]), ok ? sv + (tb | R.cit_addr[k]) : sv, ok ? 16u : 0u);
+                    }
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.landed[s]))
+                             : "memory");
             }
-            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.landed[s]))
-                         : "memory");
+        } else {
+            // thread c takes amplitude pair c of all 64 members (a warp load is 32
+            // consecutive pairs of one member: 512 contiguous bytes once the lowest target
+            // is 6 or more); with IL, thread t takes pairs c' and c' + 32
+            // (c' = t % g + (t / 2g) g) of the members with bit 0 = (t / g) % 2
+            const int g = 1 << lg;
+            const int c0 = IL ? (tid & (g - 1)) + ((tid >> (lg + 1)) << lg) : tid;
+            const uint64_t pc0 = col_base((uint64_t)(2 * c0), G);
+            const uint64_t pc1 = col_base((uint64_t)(2 * (c0 + 32)), G);
+            const bool ok0 = (uint64_t)(2 * c0) < G.n_cols, ok1 = (uint64_t)(2 * (c0 + 32)) < G.n_cols;
+            const int mb = IL ? (tid >> lg) & 1 : 0;
+            const uint64_t offb = IL ? G.off[mb] : 0;
+            for (uint64_t t = blockIdx.x; t < ntl; t += gridDim.x, ++i) {
+                const int s = i % kStages3, u = i / kStages3;
+                if (u >= 1 && !mbar_wait(smem_u32(&S.empty[s]), (u - 1) & 1, abort_flag, d_err)) break;
+                const uint64_t tb = col_base(t * kNT3, G);
+                const uint32_t sb = sB0 + (uint32_t)(s * kB3);
+                if constexpr (IL) {
+                    const uint64_t b0 = tb | pc0 | offb, b1 = tb | pc1 | offb;
+#pragma unroll 8
+                    for (int m = 0; m < 32; ++m) {
+                        const int l = 2 * m + mb;
+                        const uint64_t om = G.off[2 * m];
+                        cp_async16(sb + mn_chunk(l, c0), ok0 ? sv + (b0 | om) : sv, ok0 ? 16u : 0u);
+                        cp_async16(sb + mn_chunk(l, c0 + 32), ok1 ? sv + (b1 | om) : sv, ok1 ? 16u : 0u);
+                    }
+                } else {
+                    const uint64_t b0 = tb | pc0;
+#pragma unroll 16
+                    for (int l = 0; l < 64; ++l)
+                        cp_async16(sb + mn_chunk(l, c0), ok0 ? sv + (b0 | G.off[l]) : sv, ok0 ? 16u : 0u);
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.landed[s]))
+                             : "memory");
+            }
         }
         // every copy this thread issued has landed before the CTA may exit
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -664,7 +742,23 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
             const int s = i % kStages3;
             if (!mbar_wait(smem_u32(&S.landed[s]), (i / kStages3) & 1, abort_flag, d_err)) break;
             const uint32_t sb = sB0 + (uint32_t)(s * kB3);
-            if constexpr (P == TF32) {
+            if constexpr (P == TF32 && T0) {
+                // rows 2m, 2m + 1 hold members (2m, 2m + 1) of columns 2p and 2p + 1:
+                // trade the 8-byte halves so that each row holds its own member
+#pragma unroll 4
+                for (int m = 16 * (rt >> 6); m < 16 * (rt >> 6) + 16; ++m) {
+                    const uint32_t a0 = sb + mn_chunk(2 * m, rt & 63), a1 = sb + mn_chunk(2 * m + 1, rt & 63);
+                    uint32_t x0, y0, z0, w0, x1, y1, z1, w1;
+                    asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(x0), "=r"(y0), "=r"(z0), "=r"(w0) : "r"(a0));
+                    asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(x1), "=r"(y1), "=r"(z1), "=r"(w1) : "r"(a1));
+                    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a0), "r"(x0 + 0x1000u), "r"(y0 + 0x1000u),
+                                 "r"(x1 + 0x1000u), "r"(y1 + 0x1000u)
+                                 : "memory");
+                    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a1), "r"(z0 + 0x1000u), "r"(w0 + 0x1000u),
+                                 "r"(z1 + 0x1000u), "r"(w1 + 0x1000u)
+                                 : "memory");
+                }
+            } else if constexpr (P == TF32) {
 #pragma unroll 8
                 for (int r = 0; r < 32; ++r) {
                     const uint32_t a = sb + mn_chunk(2 * r + (rt >> 6), rt & 63);
@@ -676,7 +770,7 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
                 }
             } else {
 #pragma unroll 4
-                for (int k = 0; k < 16; ++k) split_atom(sb + (uint32_t)((16 * rw + k) * 1024), lane);
+                for (int k = 0; k < 16; ++k) split_atom<T0>(sb + (uint32_t)((16 * rw + k) * 1024), lane);
             }
             fence_proxy_async();
             mbar_arrive(smem_u32(&S.full[s]));
@@ -746,10 +840,15 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
         const int ew = warp - kProdWarps3;
         const int q = warp & 3, hh = ew >> 2;
         const int e = lane >> 4, j = 16 * q + (lane & 15);
-        const int cst = 32 * hh + lane;                        // amplitude pair this lane stores
+        // TABLE: this warp's 512 chunks (rows 16q .. 16q+15, pairs 32hh .. 32hh+31) in the
+        // order of RawMap; otherwise each lane stores pair cst (PLAIN) or, with IL, member
+        // bit lb and pairs 32 hh + pl and 32 hh + 16 + pl
+        const uint64_t wa = TABLE ? G.off[16 * q] | col_base((uint64_t)(64 * hh), G) | R.sl_addr[lane] : 0;
+        const uint32_t wsm = TABLE ? mn_chunk(16 * q, 32 * hh) ^ R.sl_sm[lane] : 0;
+        const uint32_t wcol = TABLE ? (uint32_t)(64 * hh) | R.sl_col[lane] : 0;
+        const int cst = 32 * hh + lane;
         const uint64_t pst = col_base((uint64_t)(2 * cst), G);
         const bool okst = (uint64_t)(2 * cst) < G.n_cols;
-        // IL: member bit 0 and pair offset of this lane, pairs 32 hh + pl and 32 hh + 16 + pl
         const int lb = (lane >> lg) & 1, pl = (lane & ((1 << lg) - 1)) + ((lane >> (lg + 1)) << lg);
         const uint64_t pst0 = IL ? col_base((uint64_t)(2 * (32 * hh + pl)), G) : 0;
         const uint64_t pst1 = IL ? col_base((uint64_t)(2 * (32 * hh + 16 + pl)), G) : 0;
@@ -780,6 +879,15 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
                         o = make_float4(r[0] - v[8 * g + 5], r[1] + v[8 * g + 4], r[2] - v[8 * g + 7],
                                         r[3] + v[8 * g + 6]);
                     }
+                    if constexpr (T0) {
+                        // back to memory order: member rows j, j ^ 1 (lanes lane, lane ^ 1)
+                        // trade halves, so the even row holds members (j, j + 1) of column 2c
+                        // and the odd row those of column 2c + 1
+                        const bool even = (lane & 1) == 0;
+                        const float s0 = __shfl_xor_sync(0xffffffffu, even ? o.z : o.x, 1);
+                        const float s1 = __shfl_xor_sync(0xffffffffu, even ? o.w : o.y, 1);
+                        o = even ? make_float4(o.x, o.y, s0, s1) : make_float4(s0, s1, o.z, o.w);
+                    }
                     // amplitude pair c of the tile, staged as one 16-byte chunk (conflict free:
                     // the 16 rows of an instruction fall in four 32-byte bank groups)
                     const int c = 32 * hh + 8 * cc + 2 * g + e;
@@ -791,24 +899,29 @@ k_tc6_raw(float2 *__restrict__ sv, TcGeom G, const uint4 *__restrict__ a_img, in
             tc_fence_before();
             mbar_arrive(smem_u32(&S.acc_empty[a]));
             __syncwarp();
-            // store: one member row per instruction, lanes on consecutive amplitude pairs
-            // (runs of 512 bytes when the lowest target is 6 or more; with IL, members
-            // l, l ^ 1 on alternate lane groups and 16 pairs). A store that scatters over
-            // 16 rows runs far below HBM bandwidth once the rows are MiB apart; these
-            // never do.
+            // store: chunk r of this lane is wsm ^ sr_sm[r] of the stage, in address order
+            // across the lanes (runs as long as the target positions allow)
 #pragma unroll 4
             for (int r = 0; r < 16; ++r) {
-                const int l = IL ? 16 * q + 2 * (r >> 1) + lb : 16 * q + r;
-                const int c = IL ? 32 * hh + 16 * (r & 1) + pl : cst;
                 float4 o;
-                asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
-                             : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
-                             : "r"(sb + mn_chunk(l, c)));
-                if constexpr (IL) {
-                    if ((uint64_t)(2 * c) < G.n_cols)
-                        *reinterpret_cast<float4 *>(sv + (tb | (r & 1 ? pst1 : pst0) | G.off[l])) = o;
+                if constexpr (TABLE) {
+                    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                                 : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
+                                 : "r"(sb + (wsm ^ R.sr_sm[r])));
+                    if ((uint64_t)(wcol | R.sr_col[r]) < G.n_cols)
+                        *reinterpret_cast<float4 *>(sv + (tb | wa | R.sr_addr[r])) = o;
                 } else {
-                    if (okst) *reinterpret_cast<float4 *>(sv + (tb | pst | G.off[l])) = o;
+                    const int l = IL ? 16 * q + 2 * (r >> 1) + lb : 16 * q + r;
+                    const int c = IL ? 32 * hh + 16 * (r & 1) + pl : cst;
+                    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                                 : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
+                                 : "r"(sb + mn_chunk(l, c)));
+                    if constexpr (IL) {
+                        if ((uint64_t)(2 * c) < G.n_cols)
+                            *reinterpret_cast<float4 *>(sv + (tb | (r & 1 ? pst1 : pst0) | G.off[l])) = o;
+                    } else {
+                        if (okst) *reinterpret_cast<float4 *>(sv + (tb | pst | G.off[l])) = o;
+                    }
                 }
             }
             mbar_arrive(smem_u32(&S.empty[s]));
@@ -917,15 +1030,117 @@ std::vector<unsigned char> build_a_image3(const double *g, sv_precision_t prec) 
     return img;
 }
 
-template <int P, bool IL>
-cudaError_t run_tc_raw(const LaunchCtx &L, float2 *sv, const TcGeom &G, const uint4 *d_a, int *d_err, int lg) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc6_raw<P, IL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+template <int P, int MODE>
+cudaError_t run_tc_raw(const LaunchCtx &L, float2 *sv, const TcGeom &G, const RawMap &R, const uint4 *d_a,
+                       int *d_err, int lg) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc6_raw<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
     if (e != cudaSuccess) return e;
     uint64_t grid = (uint64_t)L.num_sms;
     if (grid > G.n_tiles) grid = G.n_tiles;
-    k_tc6_raw<P, IL><<<(unsigned)grid, kThreads3, kSmem3, L.stream>>>(sv, G, d_a, d_err, lg);
+    k_tc6_raw<P, MODE><<<(unsigned)grid, kThreads3, kSmem3, L.stream>>>(sv, G, R, d_a, d_err, lg);
     ++*L.launches;
     return cudaGetLastError();
+}
+
+// operand byte offset of row l, amplitude pair c in a stage (the host twin of mn_chunk)
+uint32_t host_mn_chunk(int l, int c) {
+    return (uint32_t)((c >> 3) * 8192 + (l >> 3) * 1024 + (l & 7) * 128 + ((((c & 7) >> 1) ^ (l & 3)) << 5) +
+                      ((c & 1) << 4));
+}
+
+// The address-ordered chunk mapping of the raw-operand kernel for targets tpos on
+// an n-qubit state (see RawMap). Each index bit of a chunk has an amplitude
+// address bit, an operand offset and a column contribution; the bits are sorted
+// by address bit and dealt out to lanes first.
+RawMap build_raw_map(int n, const int *tpos, bool t0) {
+    std::vector<int> npos;                       // non-target positions, ascending; past n for tiny states
+    for (int q = 0, t = 0; (int)npos.size() < 8; ++q) {
+        if (t < 6 && q == tpos[t]) {
+            ++t;
+            continue;
+        }
+        npos.push_back(q);
+    }
+    struct Bit { int apos; uint64_t addr; uint32_t sm; uint32_t col; };
+    auto member_bit = [&](int i) {      // member index bit i (row bit i with qubit 0 free)
+        return Bit{tpos[i], 1ull << tpos[i], host_mn_chunk(1 << i, 0), 0u};
+    };
+    std::vector<Bit> copy, store;
+    if (!t0) {
+        for (int i = 0; i < 6; ++i)     // pair bit i: column bit i + 1
+            copy.push_back(Bit{npos[i + 1], 1ull << npos[i + 1], host_mn_chunk(0, 1 << i), 2u << i});
+        for (int i = 0; i < 6; ++i) copy.push_back(member_bit(i));
+        for (int i = 0; i < 5; ++i)
+            store.push_back(Bit{npos[i + 1], 1ull << npos[i + 1], host_mn_chunk(0, 1 << i), 2u << i});
+        for (int i = 0; i < 4; ++i) store.push_back(member_bit(i));
+    } else {
+        // member-pair bit i (member bit i + 1, row bit i + 1); column bit 0 selects the
+        // row of the pair, column bit i >= 1 is pair bit i - 1
+        auto pair_bit = [&](int i) {
+            return Bit{tpos[i + 1], 1ull << tpos[i + 1], host_mn_chunk(2 << i, 0), 0u};
+        };
+        auto col_bit = [&](int i) {
+            return Bit{npos[i], 1ull << npos[i], i == 0 ? host_mn_chunk(1, 0) : host_mn_chunk(0, 1 << (i - 1)), 1u << i};
+        };
+        for (int i = 0; i < 5; ++i) copy.push_back(pair_bit(i));
+        for (int i = 0; i < 7; ++i) copy.push_back(col_bit(i));
+        for (int i = 0; i < 3; ++i) store.push_back(pair_bit(i));
+        for (int i = 0; i < 6; ++i) store.push_back(col_bit(i));
+    }
+    // Address order, except that lanes 0-2 (the eight lanes of one shared-memory
+    // wavefront of 16-byte accesses) take the lowest bits whose operand offsets
+    // fall in independent 16-byte bank groups, so that those accesses never
+    // conflict; the other bits follow in address order.
+    auto order = [](std::vector<Bit> &bits) {
+        std::sort(bits.begin(), bits.end(), [](const Bit &a, const Bit &b) { return a.apos < b.apos; });
+        std::vector<Bit> out;
+        std::vector<char> used(bits.size(), 0);
+        uint32_t span = 1;                        // bank groups reachable: bit set of a subspace of GF(2)^3
+        for (size_t i = 0; i < bits.size() && out.size() < 3; ++i) {
+            const uint32_t g = (bits[i].sm >> 4) & 7u;
+            if ((span >> g) & 1u) continue;       // g is 0 or already in the span
+            uint32_t next = span;
+            for (uint32_t v = 0; v < 8; ++v)
+                if ((span >> v) & 1u) next |= 1u << (v ^ g);
+            span = next;
+            out.push_back(bits[i]);
+            used[i] = 1;
+        }
+        for (size_t i = 0; i < bits.size(); ++i)
+            if (!used[i]) out.push_back(bits[i]);
+        bits = out;
+    };
+    if (!t0 && tpos[0] >= 3) {
+        // qubits 0-2 free: pair bits across the lanes (each instruction 32 consecutive
+        // amplitude pairs of one member), member bits across a thread's copies -- the
+        // order that measured fastest there (10.8 ms per 32-qubit block against 11.4
+        // in address order); the bits are already in that order
+    } else {
+        order(copy);
+        order(store);
+    }
+    RawMap R{};
+    auto fill = [](const std::vector<Bit> &bits, int first, int count, uint64_t *addr, uint32_t *sm, uint32_t *col) {
+        for (int v = 0; v < (1 << count); ++v) {
+            uint64_t a = 0;
+            uint32_t m = 0, c = 0;
+            for (int b = 0; b < count; ++b)
+                if ((v >> b) & 1) {
+                    a |= bits[first + b].addr;
+                    m ^= bits[first + b].sm;
+                    c |= bits[first + b].col;
+                }
+            addr[v] = a;
+            sm[v] = m;
+            col[v] = c;
+        }
+    };
+    fill(copy, 0, 6, R.cthr_addr, R.cthr_sm, R.cthr_col);
+    fill(copy, 6, 6, R.cit_addr, R.cit_sm, R.cit_col);
+    fill(store, 0, 5, R.sl_addr, R.sl_sm, R.sl_col);
+    fill(store, 5, 4, R.sr_addr, R.sr_sm, R.sr_col);
+    (void)n;
+    return R;
 }
 
 template <int P>
@@ -965,27 +1180,36 @@ cudaError_t launch_tc6(const LaunchCtx &L, void *sv, int n, const int *tpos, con
     G.n_tiles = (G.n_cols + kNT - 1) / kNT;
     float2 *s = reinterpret_cast<float2 *>(sv);
     const uint4 *a = reinterpret_cast<const uint4 *>(d_a);
-    // Lowest target 1 or above (qubit 0 free; then n >= 7 and a tile holds whole
-    // amplitude pairs): the raw-operand kernel, measured on GB300 (TF32, 32-qubit
-    // state) at 10.4-10.5 ms per block for lowest target 3 or more whatever the
-    // other targets, 12.7 ms at 2, 14.8 ms at 1; with qubit 0 a target the
-    // register-staged kernel below (about 16 ms).
-    if (tpos[0] >= kRawMinLowTarget && n >= 7) {
+    // Every state of 7 qubits or more (a tile then holds whole amplitude pairs or
+    // member pairs): the raw-operand kernel; a 6-qubit state: the register-staged one.
+    if (n >= 7) {
         const std::vector<unsigned char> img = build_a_image3(mat, prec);
         cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
         if (e != cudaSuccess) return e;
+        // The copy and store order by target positions (TF32, 32-qubit state, one block):
+        // qubit 0 a target -> RawMap order (14.2-16.1 ms, against 15.8-16.7 for the
+        // register-staged kernel); lowest target 1 or 2 with a second target below 6
+        // -> RawMap order ((1..6) 13.9 ms, (2..7) 11.7, against 16.8 and 13.3 in IL order);
+        // otherwise the fixed orders (lowest target 3 or more: 10.4-10.8 ms; the table
+        // loop's extra instructions per copy cost the copy warps about 13 % there).
+        const bool t0 = tpos[0] == 0;
+        const bool mapped = !t0 && tpos[0] <= 2 && tpos[1] < 6;
+        const RawMap R = t0 || mapped ? build_raw_map(n, tpos, t0) : RawMap{};
+        const bool tf = prec == SV_PREC_TF32;
+        if (t0) return tf ? run_tc_raw<TF32, RAW_T0>(L, s, G, R, a, d_err, 0) : run_tc_raw<BF16, RAW_T0>(L, s, G, R, a, d_err, 0);
+        if (mapped)
+            return tf ? run_tc_raw<TF32, RAW_MAPPED>(L, s, G, R, a, d_err, 0)
+                      : run_tc_raw<BF16, RAW_MAPPED>(L, s, G, R, a, d_err, 0);
         if (tpos[0] <= 3) {
             const int lg = tpos[0] - 1;
-            return prec == SV_PREC_TF32 ? run_tc_raw<TF32, true>(L, s, G, a, d_err, lg)
-                                        : run_tc_raw<BF16, true>(L, s, G, a, d_err, lg);
+            return tf ? run_tc_raw<TF32, RAW_IL>(L, s, G, R, a, d_err, lg) : run_tc_raw<BF16, RAW_IL>(L, s, G, R, a, d_err, lg);
         }
-        return prec == SV_PREC_TF32 ? run_tc_raw<TF32, false>(L, s, G, a, d_err, 0)
-                                    : run_tc_raw<BF16, false>(L, s, G, a, d_err, 0);
+        return tf ? run_tc_raw<TF32, RAW_PLAIN>(L, s, G, R, a, d_err, 0) : run_tc_raw<BF16, RAW_PLAIN>(L, s, G, R, a, d_err, 0);
     }
     const std::vector<unsigned char> img = build_a_image(mat, prec);
     cudaError_t e = cudaMemcpyAsync(d_a, img.data(), img.size(), cudaMemcpyHostToDevice, L.stream);
     if (e != cudaSuccess) return e;
-    // qubit 0 a target: the register-staged kernel
+    // a 6-qubit state (one column): the register-staged kernel
     return prec == SV_PREC_TF32 ? run_tc<TF32>(L, s, G, a, d_err) : run_tc<BF16>(L, s, G, a, d_err);
 }
 
