@@ -776,9 +776,11 @@ GATE_CASES = ("1:0 1:3 2:0,1 2:3,9 2:1,5 3:0,1,2 3:0,1,5 3:3,9,14 3:20,22,24 3:0
 
 def gate_table(args) -> dict:
     """Dense gates by width and target set: single launches of a random dense
-    2^k x 2^k matrix on a complex64 state, CUDA events around each launch on
-    the handle's stream, L2 flushed (a 256 MiB write) before each, median of
-    five; GB/s counts one read and one write of every amplitude."""
+    2^k x 2^k matrix on a complex64 state ("k:t0,t1,..."), or one 6-qubit block
+    on the tensor cores ("tf32:..." / "bf16:..." with six targets), CUDA events
+    around each call on the handle's stream, L2 flushed (a 256 MiB write)
+    before each, median of the timed calls; GB/s counts one read and one write
+    of every amplitude."""
     import torch
 
     from paper_2308_01999_gb300 import sv
@@ -794,25 +796,33 @@ def gate_table(args) -> dict:
     with torch.cuda.stream(stream):
         s = sv.StateVector(psi, stream)
         s.set_basis_state(0)
+        precs = {"tf32": sv.SV_PREC_TF32, "bf16": sv.SV_PREC_SPLIT_BF16}
         for case in args.gate_cases.split():
             k, ts = case.split(":")
             t = [int(x) for x in ts.split(",")]
-            assert len(t) == int(k) and max(t) < n
+            assert max(t) < n and (k in precs and len(t) == 6 or k not in precs and len(t) == int(k))
             m = gen.random_gate_dense(rng, len(t))
+            if k in precs:      # one 6-qubit block on the tensor cores
+                g = gen.Gate(tuple(t), m)
+                run = lambda: s.apply_fused([g], 6, precs[k])  # noqa: E731
+            else:
+                run = lambda: s.apply(t, m)  # noqa: E731
             for _ in range(2):
-                s.apply(t, m)
+                run()
             times = []
             for _ in range(args.gate_reps):
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                s.apply(t, m)
+                run()
                 e1.record(stream)
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
             ms = float(np.median(times))
             out["cases"][case] = {"ms": round(ms, 4), "gbs": round(16 * (1 << n) / (ms * 1e-3) / 1e9, 1),
                                   "fp32_tflops": round(8 * (1 << len(t)) * (1 << n) / (ms * 1e-3) / 1e12, 1)}
+            if k in precs:
+                out["cases"][case].pop("fp32_tflops")
         s.close()
     return out
 

@@ -289,3 +289,35 @@ def test_results_do_not_depend_on_the_rest_of_the_batch(svmod):
         alone = b.results()[0]
         assert np.array_equal(alone, together[i]), i
     b.close()
+
+
+@pytest.mark.gpu
+def test_full_batched_workload_sampled_against_the_oracle(svmod):
+    """The benchmark's whole batched workload (4096 states of 10-20 qubits,
+    6-layer ansatz, 8 Pauli strings each) in the launch configuration the
+    benchmark times (fusion width 2, windows of 4 qubits, every state on one
+    CTA): a stratified sample of 24 states, one per size step, compared with
+    the complex128 oracle one by one."""
+    import torch
+    from paper_2308_01999_gb300 import autotune
+    sv = svmod
+    orc.set_threads(0)
+    work = gen.batched_ansatz_workload(count=4096, seed=3)
+    states = [(n, g, p) for n, g, p, _ in work]
+    b = sv.Batch(torch.cuda.current_stream())
+    info = b.compile(states, fusion_width=2, window_qubits=4)
+    assert info["items"] == 4096
+    buf = torch.empty(b.state_amps, dtype=torch.complex64, device="cuda")
+    b.launch(buf)
+    res = b.results()
+    idx = autotune.stratified_sample([n for n, _, _ in states], 24)
+    worst = 0.0
+    for i in idx:
+        n, gates, paulis = states[i]
+        ref = orc.run_circuit(gates, n)
+        want = np.array([orc.expect_pauli(ref, p, list(range(n))).real for p in paulis])
+        d = np.abs(res[i] - want)
+        worst = max(worst, float(d.max()))
+        assert np.all(d <= 1e-6 * np.maximum(1, np.abs(want))), (i, n, res[i], want)
+    print(f"[batch 4096] {len(idx)} sampled states: max |d<P>| {worst:.3e}")
+    b.close()
