@@ -345,10 +345,14 @@ SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, 
  * with at most 2 targets on at most that many local qubits applied to
  * amplitudes held in registers, one shared-memory round trip per run (0 = no
  * windows, else 2..4; tiles under 13 qubits use narrower windows so that every
- * thread keeps a group). sv_batch_compile uses window_qubits = 4. */
+ * thread keeps a group). keep_permutations changes the fusion pass (Sec.
+ * II-B) only in which block a gate joins. sv_batch_compile uses
+ * window_qubits = 4, keep_permutations = 0. */
 typedef struct {
-    int fusion_width;     /* 1..4 */
-    int window_qubits;    /* 0, 2, 3 or 4 */
+    int fusion_width;       /* 1..4 */
+    int window_qubits;      /* 0, 2, 3 or 4 */
+    int keep_permutations;  /* 0 or 1: blocks of permutation gates (CNOT, X, ...) take no other gate, so
+                               that they stay register exchanges instead of becoming dense products */
 } sv_batch_options_t;
 
 /* sv_batch_compile with explicit options; errors as sv_batch_compile, and

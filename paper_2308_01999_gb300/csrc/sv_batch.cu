@@ -441,7 +441,7 @@ extern "C" {
 
 SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, int n_items, const sv_gate_t *gates,
                                     int n_gates_total, const int *paulis, int fusion_width) {
-    const sv_batch_options_t opt{fusion_width, svk::kBatchWinQubits};
+    const sv_batch_options_t opt{fusion_width, svk::kBatchWinQubits, 0};
     return sv_batch_compile_ex(b, items, n_items, gates, n_gates_total, paulis, &opt);
 }
 
@@ -450,9 +450,10 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
                                        const sv_batch_options_t *options) {
     if (!options) return SV_ERR_INVALID_ARGUMENT;
     const int fusion_width = options->fusion_width, window_qubits = options->window_qubits;
+    const int keep_perm = options->keep_permutations;
     if (!b || (!items && n_items > 0) || n_items < 0 || fusion_width < 1 || fusion_width > 4 ||
         (n_gates_total > 0 && !gates) || n_gates_total < 0 || window_qubits < 0 || window_qubits == 1 ||
-        window_qubits > svk::kBatchWinQubits)
+        window_qubits > svk::kBatchWinQubits || (keep_perm != 0 && keep_perm != 1))
         return SV_ERR_INVALID_ARGUMENT;
     b->compiled = false;
     b->items.clear();
@@ -484,7 +485,7 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
         b->state_amps = std::max<uint64_t>(b->state_amps, it.state_offset + (1ull << n));
         // fusion, then structure analysis
         std::vector<svf::Item> fused;
-        sv_status_t s = svf::fuse(gates + it.gate_begin, it.n_gates, n, fusion_width, fused);
+        sv_status_t s = svf::fuse(gates + it.gate_begin, it.n_gates, n, fusion_width, fused, 0, keep_perm != 0);
         if (s != SV_OK) return s;
         std::vector<QOp> qops;
         for (const svf::Item &f : fused) {

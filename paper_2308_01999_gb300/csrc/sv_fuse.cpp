@@ -122,8 +122,24 @@ bool gate_is_diagonal(const sv_gate_t &g) {
     return true;
 }
 
+// one nonzero in every row and column
+bool gate_is_permutation(const sv_gate_t &g) {
+    const int D = 1 << g.n_targets;
+    for (int r = 0; r < D; ++r) {
+        int nz = 0;
+        for (int c = 0; c < D; ++c) nz += g.matrix[2 * (r * D + c)] != 0.0 || g.matrix[2 * (r * D + c) + 1] != 0.0;
+        if (nz != 1) return false;
+    }
+    for (int c = 0; c < D; ++c) {
+        int nz = 0;
+        for (int r = 0; r < D; ++r) nz += g.matrix[2 * (r * D + c)] != 0.0 || g.matrix[2 * (r * D + c) + 1] != 0.0;
+        if (nz != 1) return false;
+    }
+    return true;
+}
+
 sv_status_t fuse(const sv_gate_t *gates, int n_gates, int n_qubits, int width, std::vector<Item> &out,
-                 int diag_width) {
+                 int diag_width, bool keep_permutations) {
     out.clear();
     if (width < 1 || width > SV_MAX_TARGETS || n_qubits < 1 || n_qubits > SV_MAX_QUBITS || n_gates < 0 ||
         diag_width < 0 || diag_width > SV_MAX_TARGETS)
@@ -184,11 +200,13 @@ sv_status_t fuse(const sv_gate_t *gates, int n_gates, int n_qubits, int width, s
             for (int q : Q) last[q] = last_nd[q] = (int)out.size() - 1;
             continue;
         }
+        const bool perm = keep_permutations && gate_is_permutation(g);
         int best = -1, best_growth = 1 << 30;
         const int lo = std::max({L, 0, (int)out.size() - kScan});
         for (int j = (int)out.size() - 1; j >= lo; --j) {
             const Item &b = out[j];
             if (b.passthrough || b.diagonal) continue;
+            if (keep_permutations && b.perm_only && b.n_gates > 0 && !perm) continue;
             const int gr = growth_of(b, Q);
             if ((int)b.qubits.size() + gr <= width && gr < best_growth) {
                 best = j;
@@ -197,6 +215,7 @@ sv_status_t fuse(const sv_gate_t *gates, int n_gates, int n_qubits, int width, s
         }
         if (best < 0) best = new_block(Q, false);
         absorb(out[best], g);
+        out[best].perm_only = out[best].perm_only && perm;
         for (int q : Q) last[q] = last_nd[q] = best;
     }
     return SV_OK;

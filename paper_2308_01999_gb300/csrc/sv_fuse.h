@@ -20,6 +20,7 @@ struct Item {
     std::vector<cd> m;           // 2^k x 2^k row-major, k = qubits.size()
     int n_gates = 0;             // gates absorbed
     bool diagonal = false;       // a block of diagonal gates only (its matrix is diagonal)
+    bool perm_only = true;       // every absorbed gate is a generalized permutation
 };
 
 // Greedy fusion in program order. A gate joins the open block that needs the
@@ -33,8 +34,14 @@ struct Item {
 // diagonal matrices commute, such a gate may join any diagonal block after the
 // last non-diagonal item touching its qubits. Dense blocks then take only the
 // other gates.
+//
+// With keep_permutations, a block that holds only generalized-permutation
+// gates (CNOT, X, SWAP and the like) takes no other gate: an engine that
+// applies permutations as register exchanges then keeps them free instead of
+// paying a dense product for them (a later rotation opens or joins another
+// block). Permutation gates may still join dense blocks.
 sv_status_t fuse(const sv_gate_t *gates, int n_gates, int n_qubits, int width, std::vector<Item> &out,
-                 int diag_width = 0);
+                 int diag_width = 0, bool keep_permutations = false);
 
 // psi <- G psi for a (controlled) k-qubit gate on an s-qubit vector (host, FP64);
 // used to compose block matrices column by column.

@@ -93,9 +93,46 @@ def test_compile_on_host_only(svmod):
     b.close()
 
 
+def test_keep_permutations_rule_on_host(svmod):
+    """With keep_permutations, a fused block that holds a CNOT, X or other
+    permutation takes no dense gate: a ladder of CNOTs between layers of Haar
+    gates then fuses to more ops, dense ones only where dense gates meet, and
+    an option value other than 0 or 1 is rejected."""
+    import ctypes as C
+    sv = svmod
+    rng = gen.rng_for(8)
+    x = np.array([[0, 1], [1, 0]], dtype=complex)
+    n = 12
+    gates = []
+    for _ in range(4):
+        gates += [gen.Gate((q,), gen.haar_su2(rng)) for q in range(n)]
+        gates += [gen.Gate((q + 1,), x, (q,), (1,)) for q in range(n - 1)]
+    prog = [(n, gates, np.zeros((0, n)))]
+    ops = {}
+    for keep in (False, True):
+        b = sv.Batch()
+        ops[keep] = b.compile(prog, 2, 0, keep)["ops"]
+        assert b.choice == (2, 0, int(keep))
+        b.close()
+    assert ops[True] > ops[False]
+    packed = sv.pack_batch(prog)
+    h = C.c_void_p()
+    assert sv.lib().sv_batch_create(None, C.byref(h)) == 0
+    try:
+        for bad in ((2, 4, 2), (2, 4, -1)):
+            opt = (C.c_int * 3)(*bad)
+            rc = sv.lib().sv_batch_compile_ex(h, C.c_void_p(packed.items.ctypes.data), len(packed.items),
+                                              C.c_void_p(packed.gate_rec.ctypes.data), len(packed.gate_rec),
+                                              None, C.cast(opt, C.c_void_p))
+            assert rc == 1, (bad, rc)                  # SV_ERR_INVALID_ARGUMENT
+    finally:
+        sv.lib().sv_batch_destroy(h)
+
+
 @pytest.mark.gpu
-@pytest.mark.parametrize("width,window", [(1, 4), (2, 4), (3, 4), (4, 4), (1, 0), (2, 2), (1, 3)])
-def test_batch_matches_oracle(svmod, width, window):
+@pytest.mark.parametrize("width,window,keep", [(1, 4, 0), (2, 4, 0), (3, 4, 0), (4, 4, 0), (1, 0, 0), (2, 2, 0),
+                                               (1, 3, 0), (2, 4, 1), (3, 4, 1), (2, 3, 1), (4, 0, 1)])
+def test_batch_matches_oracle(svmod, width, window, keep):
     import torch
     sv = svmod
     # every fourth state (i % 4 == 3) is the permutation mix; the 15- and
@@ -103,7 +140,7 @@ def test_batch_matches_oracle(svmod, width, window):
     sizes = [1, 2, 5, 10, 12, 13, 14, 15, 16, 17, 18, 4, 11, 14, 16, 13, 12, 20]
     states = _mixed_states(10 + width, sizes)
     b = sv.Batch(torch.cuda.current_stream())
-    b.compile(states, fusion_width=width, window_qubits=window)
+    b.compile(states, fusion_width=width, window_qubits=window, keep_permutations=bool(keep))
     buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
     b.launch(buf, keep_states=True)
     res = b.results()
@@ -254,9 +291,9 @@ def test_large_states_split_over_the_gpu_match_the_oracle(svmod):
     sizes = [21, 12, 15, 24, 16, 9, 22]
     states = _mixed_states(2024, sizes, strings=6)
     refs = [orc.run_circuit(g, n) for n, g, _ in states]
-    for width, window in ((2, 4), (1, 0), (3, 3)):
+    for width, window, keep in ((2, 4, 0), (1, 0, 0), (3, 3, 0), (2, 4, 1)):
         b = sv.Batch(torch.cuda.current_stream())
-        b.compile(states, fusion_width=width, window_qubits=window)
+        b.compile(states, fusion_width=width, window_qubits=window, keep_permutations=bool(keep))
         buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
         b.launch(buf, keep_states=True)
         res = b.results()
