@@ -562,19 +562,22 @@ def batch_section(args) -> dict:
         if args.batch_widths:
             # fixed widths, no tuning (profiling captures of one configuration)
             parts = [int(x) for x in args.batch_widths.split(",")]
-            fw, win, keep = parts[0], parts[1], (parts[2] if len(parts) > 2 else 0)
-            info = b.compile(packed, fw, win, bool(keep))
-            out["autotune"] = {"fixed": {"fusion_width": fw, "window_qubits": win, "keep_permutations": keep}}
+            fw, win = parts[0], parts[1]
+            keep = parts[2] if len(parts) > 2 else 0
+            tile = parts[3] if len(parts) > 3 else sv.SV_BATCH_TILE_QUBITS
+            info = b.compile(packed, fw, win, bool(keep), tile)
+            out["autotune"] = {"fixed": {"fusion_width": fw, "window_qubits": win, "keep_permutations": keep,
+                                         "tile_qubits": tile}}
         else:
             tuner = autotune.BatchTuner(autotune.gpu_timer(stream), sample=args.tune_sample)
             info = b.compile(packed, tuner=tuner)            # the product path: tuned, then compiled
             sig = autotune.signature(packed.ns, packed.gate_counts)
             out["autotune"] = {"sample_states": min(args.tune_sample, len(states)), "signature": list(sig),
                                "choice": {"fusion_width": b.choice[0], "window_qubits": b.choice[1],
-                                          "keep_permutations": b.choice[2]},
-                               "sample_ms": {f"fusion{fw}_window{win}" + ("_keepperm" if kp else ""):
-                                             round(t * 1e3, 3)
-                                             for (fw, win, kp), t in tuner.timings[sig].items()}}
+                                          "keep_permutations": b.choice[2], "tile_qubits": b.choice[3]},
+                               "sample_ms": {f"fusion{fw}_window{win}" + ("_keepperm" if kp else "") +
+                                             f"_tile{tile}": round(t * 1e3, 3)
+                                             for (fw, win, kp, tile), t in tuner.timings[sig].items()}}
         out["tune_and_compile_s"] = round(time.perf_counter() - t0, 2)
         out["ops"], out["stages"] = info["ops"], info["stages"]
         buf = torch.empty(b.state_amps, dtype=torch.complex64, device=dev)
@@ -758,7 +761,7 @@ def serve_section(args) -> dict:
                              "larger": "one fused call each (native, width 4), 4 concurrent streams",
                              "batch_slots_per_class": 2},
            "batch_widths": {"fusion_width": ex.batch_widths[0], "window_qubits": ex.batch_widths[1],
-                            "keep_permutations": ex.batch_widths[2]},
+                            "keep_permutations": ex.batch_widths[2], "tile_qubits": ex.batch_widths[3]},
            "sample_note": (f"{args.serve_requests} requests of the 10000-request trace at the offered rate: "
                            "the offered load is far above one GPU's capacity, so the trace is a backlog drain "
                            "whose length only scales the makespan, and 10000 requests would hold the GPU for "
@@ -961,7 +964,7 @@ def main():
     ap.add_argument("--batch-states", type=int, default=4096, help="batch: number of states")
     ap.add_argument("--plain-sample", type=int, default=256, help="batch: states run through the plain engine")
     ap.add_argument("--tune-sample", type=int, default=1024, help="batch: states the autotuner times")
-    ap.add_argument("--batch-widths", default="", help="batch: 'fusion,window[,keep_permutations]' instead of the autotuner")
+    ap.add_argument("--batch-widths", default="", help="batch: 'fusion,window[,keep_permutations[,tile_qubits]]' instead of the autotuner")
     ap.add_argument("--gate-cases", default=GATE_CASES, help="gates: 'k:t0,t1,..' cases, space separated")
     ap.add_argument("--gate-reps", type=int, default=5, help="gates: timed launches per case")
     ap.add_argument("--main-only", action="store_true",

@@ -234,7 +234,7 @@ SV_API sv_status_t sv_expectation_pauli(sv_handle_t h, const int *paulis, const 
  * SV_NOALLOC_MAX_STRINGS strings per call (more: SV_ERR_INSUFFICIENT_WORKSPACE,
  * before any work is enqueued). The first call on a device, made with that
  * device current, looks up the array's device address (cudaGetSymbolAddress)
- * and caches it: make that first call before any stream capture. All calls
+ * and caches it. All calls
  * share the array: calls whose work overlaps on the GPU race, so the caller
  * must order them (one stream, or synchronise between them). Synchronises the
  * stream. Errors: INVALID_ARGUMENT as sv_expectation_pauli, or for a NULL or
@@ -333,8 +333,9 @@ SV_API sv_status_t sv_batch_destroy(sv_batch_t b);
 /* Compile the batch on the host (no GPU work): per state, greedy fusion into
  * blocks of at most fusion_width (1..4) qubits, exact structure analysis
  * (controls, diagonal, generalized permutation, dense), and passes of at most
- * 14 local qubits. Each gate: 1..4 targets, at most 8 controls, all qubits
- * distinct and < n_qubits, targets + controls <= min(n_qubits, 14).
+ * 14 local qubits (sv_batch_compile_ex: tile_qubits). Each gate: 1..4
+ * targets, at most 8 controls, all qubits distinct and < n_qubits,
+ * targets + controls <= min(n_qubits, 14).
  * Errors: INVALID_ARGUMENT for any bad field; NOT_SUPPORTED for a fused block
  * the batch kernel cannot take. Replaces any previous program. */
 SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, int n_items,
@@ -346,13 +347,18 @@ SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, 
  * amplitudes held in registers, one shared-memory round trip per run (0 = no
  * windows, else 2..4; tiles under 13 qubits use narrower windows so that every
  * thread keeps a group). keep_permutations changes the fusion pass (Sec.
- * II-B) only in which block a gate joins. sv_batch_compile uses
- * window_qubits = 4, keep_permutations = 0. */
+ * II-B) only in which block a gate joins. tile_qubits is the number of local
+ * qubits of a pass: a state of at most that many qubits stays in shared
+ * memory for its whole circuit, a larger one is processed in passes over
+ * 2^tile_qubits-amplitude tiles, and every gate's targets + controls must
+ * not exceed min(n_qubits, tile_qubits). sv_batch_compile uses
+ * window_qubits = 4, keep_permutations = 0, tile_qubits = 14. */
 typedef struct {
     int fusion_width;       /* 1..4 */
     int window_qubits;      /* 0, 2, 3 or 4 */
     int keep_permutations;  /* 0 or 1: blocks of permutation gates (CNOT, X, ...) take no other gate, so
                                that they stay register exchanges instead of becoming dense products */
+    int tile_qubits;        /* 10..SV_BATCH_TILE_QUBITS */
 } sv_batch_options_t;
 
 /* sv_batch_compile with explicit options; errors as sv_batch_compile, and

@@ -1,14 +1,15 @@
 """Autotuner of the batched engine's compile options.
 
-The batched engine (``sv.Batch``) has three knobs that trade host-side fusion
+The batched engine (``sv.Batch``) has four knobs that trade host-side fusion
 against on-chip work: the gate-fusion width (blocks of 1-4 qubits, Sec. II-B),
 the register-window width (runs of small ops applied to 2^w amplitudes held in
-registers, 0 = off) and the keep-permutations fusion rule (blocks of CNOTs and
-other permutations take no dense gate, so they stay register exchanges).
+registers, 0 = off), the keep-permutations fusion rule (blocks of CNOTs and
+other permutations take no dense gate, so they stay register exchanges) and
+the tile size (local qubits of a pass over a state held in shared memory).
 Which combination is fastest depends on the workload's
 qubit counts and circuit depth, so the tuner measures it: it compiles a
 stratified sample of the batch (every k-th state in order of qubit count, so
-the sample keeps the workload's size mix) with each candidate pair, times one
+the sample keeps the workload's size mix) with each candidate, times one
 launch of each on the device, keeps the fastest, and caches the choice under
 a coarse workload signature (qubit range and gates per qubit), so batches of
 the same kind of work reuse it without timing again.
@@ -25,9 +26,10 @@ import numpy as np
 
 __all__ = ["CANDIDATES", "signature", "stratified_sample", "BatchTuner", "gpu_timer", "default_tuner"]
 
-# (fusion width, window width, keep permutations)
-CANDIDATES: Tuple[Tuple[int, int, int], ...] = ((1, 4, 0), (2, 4, 0), (2, 4, 1), (3, 4, 0), (3, 4, 1), (4, 4, 0),
-                                                (1, 3, 0), (2, 3, 0), (2, 3, 1), (1, 0, 0), (2, 0, 0))
+# (fusion width, window width, keep permutations, tile qubits)
+CANDIDATES: Tuple[Tuple[int, int, int, int], ...] = (
+    (1, 4, 0, 14), (2, 4, 0, 14), (2, 4, 1, 14), (3, 4, 0, 14), (3, 4, 1, 14), (4, 4, 0, 14),
+    (1, 3, 0, 14), (2, 3, 0, 14), (2, 3, 1, 14), (1, 0, 0, 14), (2, 0, 0, 14), (2, 4, 0, 13), (2, 3, 0, 12))
 
 
 def signature(ns: Sequence[int], gate_counts: Sequence[int]) -> tuple:
@@ -51,22 +53,24 @@ def stratified_sample(ns: Sequence[int], k: int) -> list:
 
 
 class BatchTuner:
-    """Chooses (fusion width, window width, keep permutations) for a batch by
-    timing candidates.
+    """Chooses (fusion width, window width, keep permutations, tile qubits) for
+    a batch by timing candidates.
 
-    timer(packed_sample, fusion_width, window_qubits, keep_permutations) ->
-    seconds (or any monotone cost). ``choose`` returns the cached choice for the batch's
-    signature, timing the candidates on a stratified sample the first time."""
+    timer(packed_sample, fusion_width, window_qubits, keep_permutations,
+    tile_qubits) -> seconds (or any monotone cost). ``choose`` returns the
+    cached choice for the batch's signature, timing the candidates on a
+    stratified sample the first time."""
 
-    def __init__(self, timer: Callable, candidates: Sequence[Tuple[int, int, int]] = CANDIDATES, sample: int = 1024):
+    def __init__(self, timer: Callable, candidates: Sequence[Tuple[int, int, int, int]] = CANDIDATES,
+                 sample: int = 1024):
         self.timer = timer
         self.candidates = tuple(candidates)
         self.sample = int(sample)
-        self.cache: Dict[tuple, Tuple[int, int, int]] = {}
-        self.timings: Dict[tuple, Dict[Tuple[int, int, int], float]] = {}
+        self.cache: Dict[tuple, Tuple[int, int, int, int]] = {}
+        self.timings: Dict[tuple, Dict[Tuple[int, int, int, int], float]] = {}
         self._lock = threading.Lock()
 
-    def choose(self, packed) -> Tuple[int, int, int]:
+    def choose(self, packed) -> Tuple[int, int, int, int]:
         from . import sv
         sig = signature(packed.ns, packed.gate_counts)
         with self._lock:
@@ -123,11 +127,11 @@ def gpu_timer(stream=None, reps: int = 2) -> Callable:
     from . import sv
     state = {"buf": None}
 
-    def timer(packed, fusion_width, window_qubits, keep_permutations=0):
+    def timer(packed, fusion_width, window_qubits, keep_permutations=0, tile_qubits=sv.SV_BATCH_TILE_QUBITS):
         st = stream or torch.cuda.current_stream()
         b = sv.Batch(st)
         try:
-            b.compile(packed, fusion_width, window_qubits, bool(keep_permutations))
+            b.compile(packed, fusion_width, window_qubits, bool(keep_permutations), tile_qubits)
             buf = state["buf"]
             if buf is None or buf.numel() < b.state_amps:
                 buf = state["buf"] = torch.empty(max(1, b.state_amps), dtype=torch.complex64, device="cuda")

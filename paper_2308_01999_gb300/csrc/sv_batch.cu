@@ -57,9 +57,9 @@ struct QOp {                     // an op in global qubit numbering
     uint64_t qmask;
 };
 
-bool gate_ok(const sv_gate_t &g, int n) {
+bool gate_ok(const sv_gate_t &g, int n, int tile_qubits) {
     if (g.n_targets < 1 || g.n_targets > 4 || g.n_controls < 0 || g.n_controls > 8 || !g.matrix ||
-        g.n_targets + g.n_controls > std::min(n, svk::kBatchTileQubits))
+        g.n_targets + g.n_controls > std::min(n, tile_qubits))
         return false;
     uint64_t seen = 0;
     for (int i = 0; i < g.n_targets + g.n_controls; ++i) {
@@ -441,7 +441,7 @@ extern "C" {
 
 SV_API sv_status_t sv_batch_compile(sv_batch_t b, const sv_batch_item_t *items, int n_items, const sv_gate_t *gates,
                                     int n_gates_total, const int *paulis, int fusion_width) {
-    const sv_batch_options_t opt{fusion_width, svk::kBatchWinQubits, 0};
+    const sv_batch_options_t opt{fusion_width, svk::kBatchWinQubits, 0, svk::kBatchTileQubits};
     return sv_batch_compile_ex(b, items, n_items, gates, n_gates_total, paulis, &opt);
 }
 
@@ -450,10 +450,11 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
                                        const sv_batch_options_t *options) {
     if (!options) return SV_ERR_INVALID_ARGUMENT;
     const int fusion_width = options->fusion_width, window_qubits = options->window_qubits;
-    const int keep_perm = options->keep_permutations;
+    const int keep_perm = options->keep_permutations, tile_qubits = options->tile_qubits;
     if (!b || (!items && n_items > 0) || n_items < 0 || fusion_width < 1 || fusion_width > 4 ||
         (n_gates_total > 0 && !gates) || n_gates_total < 0 || window_qubits < 0 || window_qubits == 1 ||
-        window_qubits > svk::kBatchWinQubits || (keep_perm != 0 && keep_perm != 1))
+        window_qubits > svk::kBatchWinQubits || (keep_perm != 0 && keep_perm != 1) ||
+        tile_qubits < svk::kBatchMinTileQubits || tile_qubits > svk::kBatchTileQubits)
         return SV_ERR_INVALID_ARGUMENT;
     b->compiled = false;
     b->items.clear();
@@ -480,7 +481,7 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
             (it.n_strings > 0 && (!paulis || it.pauli_begin < 0)))
             return SV_ERR_INVALID_ARGUMENT;
         for (int g = 0; g < it.n_gates; ++g)
-            if (!gate_ok(gates[it.gate_begin + g], n)) return SV_ERR_INVALID_ARGUMENT;
+            if (!gate_ok(gates[it.gate_begin + g], n, tile_qubits)) return SV_ERR_INVALID_ARGUMENT;
         b->n_out = std::max(b->n_out, it.out_begin + it.n_strings);
         b->state_amps = std::max<uint64_t>(b->state_amps, it.state_offset + (1ull << n));
         // fusion, then structure analysis
@@ -505,7 +506,7 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
             if (!classify(g, qops)) return SV_ERR_NOT_SUPPORTED;
         }
         // stages of at most T local qubits
-        const int T = std::min(n, svk::kBatchTileQubits);
+        const int T = std::min(n, tile_qubits);
         struct St { uint64_t q; std::vector<int> ops; };
         std::vector<St> sts;
         std::vector<int> last(n, -1);

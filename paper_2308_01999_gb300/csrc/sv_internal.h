@@ -95,11 +95,12 @@ cudaError_t launch_wait_probe(const LaunchCtx &L, int *d_err, long long cycles);
 // ---- batched small states (k_batch.cu, sv_batch.cu) ----
 // One persistent launch advances many independent states. Each state's gates
 // are compiled into ops on local bit positions of a tile of 2^T amplitudes
-// (T = min(n, kBatchTileQubits)) and grouped into stages: a stage names T
+// (T = min(n, the compile's tile size <= kBatchTileQubits)) and grouped into stages: a stage names T
 // "local" qubits (lmask) and its ops act on local qubits only, so one pass
 // over the state -- 2^(n-T) tiles, each gathered into shared memory once --
 // applies all of them.
 constexpr int kBatchTileQubits = 14;
+constexpr int kBatchMinTileQubits = 10;   // smallest tile a compile option may ask for (2 amplitudes a thread)
 constexpr int kBatchThreads = 512;
 enum BatchOpKind { BOP_DENSE = 0, BOP_DIAG = 1, BOP_PERM = 2, BOP_WIN = 3 };
 // A window (BOP_WIN) applies a run of small ops to amplitudes held in registers:
@@ -163,7 +164,7 @@ struct BStr {
 };
 
 // The persistent kernel's work list, taken in order from an atomic counter.
-// A state of at most kBatchTileQubits qubits is one BT_STATE task (its whole
+// A state of at most T qubits is one BT_STATE task (its whole
 // circuit in shared memory). A larger state is either one BT_WHOLE task (one
 // CTA runs every pass and the expectation sums, so the state stays warm in L2
 // between its passes) or, when it holds more work than one CTA's share of the

@@ -14,7 +14,7 @@
 // Host code must not use the array's name as a device address (on the host it
 // names a host-side stand-in). The device address is looked up once per device,
 // with that device current, on the first call made there (cudaGetSymbolAddress),
-// and cached; that first call should therefore come before any stream capture.
+// and cached.
 //
 // Every call shares the one array, and it keeps the contents of the last call.
 // Nothing in it needs to start at zero: each block writes its partial sums

@@ -453,6 +453,8 @@ class StateVector:
 
 SV_BATCH_KEEP_STATES = 1
 SV_BATCH_CHECK_WAIT = 2
+SV_BATCH_MAX_QUBITS = 26
+SV_BATCH_TILE_QUBITS = 14     # largest (and default) tile: local qubits of one pass
 GATE_DTYPE = np.dtype([("n_targets", "<i4"), ("targets", "<i4", (SV_MAX_TARGETS,)), ("n_controls", "<i4"),
                        ("controls", "<i4", (SV_MAX_CONTROLS,)), ("control_values", "<i4", (SV_MAX_CONTROLS,)),
                        ("matrix", "<u8")])
@@ -514,13 +516,14 @@ def sv_batch_compile(b: int, items: np.ndarray, gate_rec: np.ndarray, paulis: np
 
 
 def sv_batch_compile_ex(b: int, items: np.ndarray, gate_rec: np.ndarray, paulis: np.ndarray, fusion_width: int,
-                        window_qubits: int, keep_permutations: bool = False):
-    """sv_batch_compile with the register-window width (0, 2, 3 or 4) and the
-    keep-permutations fusion rule as options."""
+                        window_qubits: int, keep_permutations: bool = False, tile_qubits: int = SV_BATCH_TILE_QUBITS):
+    """sv_batch_compile with the register-window width (0, 2, 3 or 4), the
+    keep-permutations fusion rule and the tile size (local qubits of a pass,
+    10..14) as options."""
     items = np.ascontiguousarray(items, dtype=ITEM_DTYPE)
     gate_rec = np.ascontiguousarray(gate_rec, dtype=GATE_DTYPE)
     paulis = np.ascontiguousarray(paulis, dtype=np.int32).reshape(-1)
-    opt = (C.c_int * 3)(int(fusion_width), int(window_qubits), int(bool(keep_permutations)))
+    opt = (C.c_int * 4)(int(fusion_width), int(window_qubits), int(bool(keep_permutations)), int(tile_qubits))
     _check(lib().sv_batch_compile_ex(_VP(b), _VP(items.ctypes.data), int(items.size), _VP(gate_rec.ctypes.data),
                                      int(gate_rec.size), paulis.ctypes.data_as(_I) if paulis.size else None,
                                      C.cast(opt, _VP)), "sv_batch_compile_ex")
@@ -608,23 +611,23 @@ class Batch:
         self.choice = None
 
     def compile(self, states, fusion_width: int = 2, window_qubits: int = 4, keep_permutations: bool = False,
-                autotune: bool = False, tuner=None, state_offsets=None):
+                tile_qubits: int = SV_BATCH_TILE_QUBITS, autotune: bool = False, tuner=None, state_offsets=None):
         """Compile on the host. With autotune (or a tuner given), the fusion width,
-        window width and fusion rule come from the tuner (``autotune.BatchTuner``),
-        which times its candidates on a sample of these states once per workload
-        signature."""
+        window width, fusion rule and tile size come from the tuner
+        (``autotune.BatchTuner``), which times its candidates on a sample of
+        these states once per workload signature."""
         packed = states if isinstance(states, PackedBatch) else pack_batch(states, state_offsets)
         if autotune or tuner is not None:
             from .autotune import default_tuner
             tuner = tuner or default_tuner(self.stream)
-            fusion_width, window_qubits, keep_permutations = tuner.choose(packed)
+            fusion_width, window_qubits, keep_permutations, tile_qubits = tuner.choose(packed)
         sv_batch_compile_ex(self.handle, packed.items, packed.gate_rec, packed.paulis, fusion_width, window_qubits,
-                            keep_permutations)
+                            keep_permutations, tile_qubits)
         self._keep = packed
         self.n_out = packed.n_out
         self.state_amps = packed.state_amps
         self.offsets = packed.offsets
-        self.choice = (int(fusion_width), int(window_qubits), int(bool(keep_permutations)))
+        self.choice = (int(fusion_width), int(window_qubits), int(bool(keep_permutations)), int(tile_qubits))
         return self.info()
 
     def info(self):

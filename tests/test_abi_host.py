@@ -36,6 +36,16 @@ def test_library_exports_every_declared_entry_point(sv):
     assert sorted(sv.EXPORTED) == declared
 
 
+def test_binding_constants_match_the_header(sv):
+    """Every #define of include/sv.h that the binding restates has the same value."""
+    text = open(os.path.join(ROOT, "include", "sv.h")).read()
+    defines = {k: int(v) for k, v in re.findall(r"^#define\s+(SV_\w+)\s+(\d+)\b", text, flags=re.M)}
+    shared = [k for k in defines if hasattr(sv, k)]
+    assert {"SV_BATCH_MAX_QUBITS", "SV_BATCH_TILE_QUBITS", "SV_BATCH_KEEP_STATES", "SV_BATCH_CHECK_WAIT"} <= set(shared)
+    for k in shared:
+        assert getattr(sv, k) == defines[k], k
+
+
 def test_status_strings(sv):
     assert sv.sv_status_string(0) == "SV_OK"
     assert sv.sv_status_string(1) == "SV_ERR_INVALID_ARGUMENT"

@@ -26,22 +26,22 @@ def test_keeps_the_fastest_candidate_and_caches_it(mods):
     autotune, sv = mods
     calls = []
 
-    def fake_timer(sub, fw, win, keep):
-        calls.append((fw, win, keep, len(sub.ns)))
+    def fake_timer(sub, fw, win, keep, tile):
+        calls.append((fw, win, keep, tile, len(sub.ns)))
         b = sv.Batch(None)                    # the sample really compiles
-        b.compile(sub, fw, win, bool(keep))
+        b.compile(sub, fw, win, bool(keep), tile)
         b.close()
-        return {(3, 4, 1): 1.0, (1, 0, 0): 1.5}.get((fw, win, keep), 2.0 + 0.1 * fw)
+        return {(3, 4, 1, 14): 1.0, (1, 0, 0, 14): 1.5}.get((fw, win, keep, tile), 2.0 + 0.1 * fw)
 
     tuner = autotune.BatchTuner(fake_timer, sample=40)
     packed = sv.pack_batch(_states(120, 1))
-    assert tuner.choose(packed) == (3, 4, 1)
-    assert [c[:3] for c in calls] == list(autotune.CANDIDATES)
-    assert all(c[3] == 40 for c in calls)
+    assert tuner.choose(packed) == (3, 4, 1, 14)
+    assert [c[:4] for c in calls] == list(autotune.CANDIDATES)
+    assert all(c[4] == 40 for c in calls)
     # another batch of the same kind: cached, nothing timed
     again = sv.pack_batch(_states(90, 2))
     assert autotune.signature(again.ns, again.gate_counts) == autotune.signature(packed.ns, packed.gate_counts)
-    assert tuner.choose(again) == (3, 4, 1) and len(calls) == len(autotune.CANDIDATES)
+    assert tuner.choose(again) == (3, 4, 1, 14) and len(calls) == len(autotune.CANDIDATES)
     # a batch of another kind (other qubit range) is timed anew
     other = sv.pack_batch(_states(30, 3, nmin=5, nmax=8))
     tuner.choose(other)
@@ -51,13 +51,13 @@ def test_keeps_the_fastest_candidate_and_caches_it(mods):
 def test_ties_go_to_the_earlier_candidate_and_rejected_options_are_skipped(mods):
     autotune, sv = mods
 
-    def timer(sub, fw, win, keep):
+    def timer(sub, fw, win, keep, tile):
         if fw == 1:
             raise sv.SvError(2, "rejected")
         return 5.0
 
     tuner = autotune.BatchTuner(timer, sample=8)
-    assert tuner.choose(sv.pack_batch(_states(20, 4))) == (2, 4, 0)
+    assert tuner.choose(sv.pack_batch(_states(20, 4))) == (2, 4, 0, 14)
 
 
 def test_stratified_sample_keeps_the_size_mix(mods):
@@ -74,9 +74,9 @@ def test_stratified_sample_keeps_the_size_mix(mods):
 
 def test_batch_compile_uses_the_tuner(mods):
     autotune, sv = mods
-    tuner = autotune.BatchTuner(lambda sub, fw, win, keep: float((fw, win, keep) == (2, 3, 1)) * -1.0 + 1.0,
-                                sample=16)
+    tuner = autotune.BatchTuner(
+        lambda sub, fw, win, keep, tile: float((fw, win, keep, tile) == (2, 3, 0, 12)) * -1.0 + 1.0, sample=16)
     b = sv.Batch(None)
     b.compile(_states(50, 5), tuner=tuner)
-    assert b.choice == (2, 3, 1)
+    assert b.choice == (2, 3, 0, 12)
     b.close()

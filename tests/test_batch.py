@@ -93,6 +93,46 @@ def test_compile_on_host_only(svmod):
     b.close()
 
 
+def test_tile_size_option_on_host(svmod):
+    """tile_qubits sets the local qubits of a pass: a state at or below it is
+    one pass, a state above it several; a tile of 12 takes register windows of
+    at most 3 qubits (2^(T - w) groups must cover the CTA), so the same
+    program needs more ops; a gate wider than the tile is rejected, and so is
+    a tile outside 10..14."""
+    import ctypes as C
+    sv = svmod
+    rng = gen.rng_for(9)
+    big = (16, gen.ansatz_circuit(16, 3, rng), np.zeros((0, 16)))
+    small = (12, gen.ansatz_circuit(12, 3, rng), np.zeros((0, 12)))
+    ops = {}
+    for tile in (14, 13, 12):
+        b = sv.Batch()
+        info = b.compile([big], 2, 4, False, tile)
+        assert b.choice == (2, 4, 0, tile) and info["stages"] >= 2
+        ops[tile] = info["ops"]
+        assert b.compile([small], 2, 4, False, tile)["stages"] == 1
+        b.close()
+    assert ops[12] > ops[14]
+    wide = (13, [gen.Gate((0, 1, 2, 3), gen.random_gate_dense(rng, 4), tuple(range(4, 13)), (1,) * 9)],
+            np.zeros((0, 13)))
+    b = sv.Batch()
+    with pytest.raises(sv.SvError):
+        b.compile([wide], 2, 4, False, 12)           # 13 qubits on one gate, tile of 12
+    b.close()
+    packed = sv.pack_batch([small])
+    h = C.c_void_p()
+    assert sv.lib().sv_batch_create(None, C.byref(h)) == 0
+    try:
+        for bad in (9, 15, 0):
+            opt = (C.c_int * 4)(2, 4, 0, bad)
+            rc = sv.lib().sv_batch_compile_ex(h, C.c_void_p(packed.items.ctypes.data), len(packed.items),
+                                              C.c_void_p(packed.gate_rec.ctypes.data), len(packed.gate_rec),
+                                              None, C.cast(opt, C.c_void_p))
+            assert rc == 1, (bad, rc)                  # SV_ERR_INVALID_ARGUMENT
+    finally:
+        sv.lib().sv_batch_destroy(h)
+
+
 def test_keep_permutations_rule_on_host(svmod):
     """With keep_permutations, a fused block that holds a CNOT, X or other
     permutation takes no dense gate: a ladder of CNOTs between layers of Haar
@@ -112,7 +152,7 @@ def test_keep_permutations_rule_on_host(svmod):
     for keep in (False, True):
         b = sv.Batch()
         ops[keep] = b.compile(prog, 2, 0, keep)["ops"]
-        assert b.choice == (2, 0, int(keep))
+        assert b.choice == (2, 0, int(keep), 14)
         b.close()
     assert ops[True] > ops[False]
     packed = sv.pack_batch(prog)
@@ -120,7 +160,7 @@ def test_keep_permutations_rule_on_host(svmod):
     assert sv.lib().sv_batch_create(None, C.byref(h)) == 0
     try:
         for bad in ((2, 4, 2), (2, 4, -1)):
-            opt = (C.c_int * 3)(*bad)
+            opt = (C.c_int * 4)(*bad, 14)
             rc = sv.lib().sv_batch_compile_ex(h, C.c_void_p(packed.items.ctypes.data), len(packed.items),
                                               C.c_void_p(packed.gate_rec.ctypes.data), len(packed.gate_rec),
                                               None, C.cast(opt, C.c_void_p))
@@ -130,9 +170,11 @@ def test_keep_permutations_rule_on_host(svmod):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("width,window,keep", [(1, 4, 0), (2, 4, 0), (3, 4, 0), (4, 4, 0), (1, 0, 0), (2, 2, 0),
-                                               (1, 3, 0), (2, 4, 1), (3, 4, 1), (2, 3, 1), (4, 0, 1)])
-def test_batch_matches_oracle(svmod, width, window, keep):
+@pytest.mark.parametrize("width,window,keep,tile", [(1, 4, 0, 14), (2, 4, 0, 14), (3, 4, 0, 14), (4, 4, 0, 14),
+                                                    (1, 0, 0, 14), (2, 2, 0, 14), (1, 3, 0, 14), (2, 4, 1, 14),
+                                                    (3, 4, 1, 14), (2, 3, 1, 14), (4, 0, 1, 14), (2, 4, 0, 13),
+                                                    (2, 3, 0, 12), (3, 4, 0, 10)])
+def test_batch_matches_oracle(svmod, width, window, keep, tile):
     import torch
     sv = svmod
     # every fourth state (i % 4 == 3) is the permutation mix; the 15- and
@@ -140,7 +182,7 @@ def test_batch_matches_oracle(svmod, width, window, keep):
     sizes = [1, 2, 5, 10, 12, 13, 14, 15, 16, 17, 18, 4, 11, 14, 16, 13, 12, 20]
     states = _mixed_states(10 + width, sizes)
     b = sv.Batch(torch.cuda.current_stream())
-    b.compile(states, fusion_width=width, window_qubits=window, keep_permutations=bool(keep))
+    b.compile(states, fusion_width=width, window_qubits=window, keep_permutations=bool(keep), tile_qubits=tile)
     buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
     b.launch(buf, keep_states=True)
     res = b.results()
@@ -291,9 +333,9 @@ def test_large_states_split_over_the_gpu_match_the_oracle(svmod):
     sizes = [21, 12, 15, 24, 16, 9, 22]
     states = _mixed_states(2024, sizes, strings=6)
     refs = [orc.run_circuit(g, n) for n, g, _ in states]
-    for width, window, keep in ((2, 4, 0), (1, 0, 0), (3, 3, 0), (2, 4, 1)):
+    for width, window, keep, tile in ((2, 4, 0, 14), (1, 0, 0, 14), (3, 3, 0, 14), (2, 4, 1, 14), (2, 3, 0, 12)):
         b = sv.Batch(torch.cuda.current_stream())
-        b.compile(states, fusion_width=width, window_qubits=window, keep_permutations=bool(keep))
+        b.compile(states, fusion_width=width, window_qubits=window, keep_permutations=bool(keep), tile_qubits=tile)
         buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
         b.launch(buf, keep_states=True)
         res = b.results()
