@@ -393,8 +393,10 @@ def run_ours(args):
     del s, psi
     torch.cuda.empty_cache()
     if world == 1 and not args.main_only:
-        # the other two parts of the headline metric, on the same GPU after the
-        # 28-qubit step (rank 0 at N = 1 only, like the CPU baseline)
+        # the 30-qubit size of the bandwidth target and the other two parts of
+        # the headline metric, on the same GPU after the 28-qubit step (rank 0
+        # at N = 1 only, like the CPU baseline)
+        line["n30"] = n30_section(args)
         line["batch"] = batch_section(args)
         line["serve"] = serve_section(args)
     print(json.dumps(line))
@@ -525,6 +527,55 @@ def run_fused(args):
         s.close()
     out["peaks"] = {"hbm_gbs": peak_hbm, "bf16_tflops": bf16_peak, "tf32_tflops_from_nominal_ratio": round(tf32_peak, 1)}
     print(json.dumps(out))
+
+
+def n30_section(args, n: int = 30) -> dict:
+    """The size of the >= 80 %-of-HBM target: one dense one-qubit SU(2) gate
+    per launch on every target qubit of a 30-qubit complex64 state (8 GiB,
+    60 times L2, so no launch finds its input in cache), two rounds over the
+    30 targets, the second timed launch by launch with CUDA events on the
+    launching stream. Algorithmic bytes per launch: one read and one write of
+    the state. The norm after the 60 gates checks that they were applied."""
+    import torch
+
+    from paper_2308_01999_gb300 import sv
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.empty_cache()
+    stream = torch.cuda.Stream(dev)
+    rng = gen.rng_for(30)
+    mats = [gen.haar_su2(rng) for _ in range(2 * n)]
+    nbytes = 2 * AMP_BYTES * (1 << n)
+    peak, kind = load_peaks()
+    with torch.cuda.stream(stream):
+        psi = torch.empty(1 << n, dtype=torch.complex64, device=dev)
+        s = sv.StateVector(psi, stream)
+        s.set_basis_state(0)
+        for q in range(n):
+            s.apply([q], mats[q])
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        clocks = Clocks(gpu_id(torch, dev))
+        torch.cuda.synchronize()
+        clocks.start()
+        for q in range(n):
+            ev[q][0].record(stream)
+            s.apply([q], mats[n + q])
+            ev[q][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        norm = s.norm2()
+        s.close()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    gbs = [nbytes / (t * 1e-3) / 1e9 for t in ms]
+    total = n * nbytes / (sum(ms) * 1e-3) / 1e9
+    del psi
+    torch.cuda.empty_cache()
+    return {"workload": f"{n}-qubit complex64 state (8 GiB), dense one-qubit SU(2) gate on each of the {n} target "
+                        "qubits, one launch each",
+            "gate_gbs": round(total, 1), "frac_of_8tbs": round(total / 8000.0, 4),
+            "frac_of_peak": round(total / peak, 4), "peak_gbs": peak, "peak_kind": kind,
+            "per_target_gbs_min": round(min(gbs), 1), "per_target_gbs_max": round(max(gbs), 1),
+            "ms_per_gate": round(sum(ms) / n, 4), "norm_minus_1": float(norm - 1.0), "clocks": clk}
 
 
 def batch_section(args) -> dict:
@@ -946,6 +997,10 @@ def run_serve(args):
     print(json.dumps(serve_section(args)))
 
 
+def run_n30(args):
+    print(json.dumps(n30_section(args)))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -955,7 +1010,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--qubits", type=int, default=28,
                     help="state size; 28 is the benchmark workload, smaller sizes are for profiling captures")
-    ap.add_argument("--workload", choices=("circuit28", "fused32", "batch", "serve", "cpu-plan", "gates"),
+    ap.add_argument("--workload", choices=("circuit28", "fused32", "batch", "serve", "n30", "cpu-plan", "gates"),
                     default="circuit28",
                     help="fused32: the 32-qubit fused brick-wall study (tensor cores, errors vs complex128)")
     ap.add_argument("--fused-qubits", type=int, default=32)
@@ -987,6 +1042,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "n30":
+        run_n30(args)
     elif args.workload == "cpu-plan":
         run_cpu_plan(args)
     elif args.workload == "gates":
