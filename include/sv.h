@@ -371,6 +371,16 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
 SV_API sv_status_t sv_batch_info(sv_batch_t b, int *n_items, int *n_stages, int *n_ops,
                                  uint64_t *state_amps, uint64_t *launches);
 
+/* What the compiled program does, counted on the host (no GPU work): entry
+ * [0] dense ops applied on their own (one pass over the tile each), [1]
+ * diagonal ops, [2] permutation ops, [3] register windows, then the windows'
+ * sub-ops: [4] 2x2 products, [5] of those, products fused with a CNOT-type
+ * exchange before or after them, [6] 4x4 products, [7] exchanges and other
+ * permutations on their own, [8] diagonals. Counts are per program (a stage
+ * that runs over many tiles counts once). */
+#define SV_BATCH_STATS 9
+SV_API sv_status_t sv_batch_program_stats(sv_batch_t b, uint64_t counts[SV_BATCH_STATS]);
+
 /* Upload the program and enqueue the one persistent kernel. d_states: device
  * memory of at least the largest state_offset + 2^n_qubits complex64
  * amplitudes, 16-byte aligned, caller-owned; states above 14 qubits always use

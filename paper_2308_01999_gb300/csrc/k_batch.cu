@@ -235,6 +235,37 @@ __device__ __forceinline__ void win_dense1_cx(float2 (&v)[1 << W], const float2 
     }
 }
 
+// the exchange across bit T where bit C == CV, then a 2x2 on bit B (B is C or
+// T): the 2x2 reads the exchanged registers
+template <int W, int B, int C, int T, int CV>
+__device__ __forceinline__ void win_cx_dense1(float2 (&v)[1 << W], const float2 *m) {
+    if constexpr (B < W && C < W && T < W && B == T) {
+        // the exchange stays within each pair: where it applies, the pair's two
+        // inputs trade places, which is the matrix with its columns exchanged
+        const float2 m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) {
+            if (r & (1 << B)) continue;
+            if (((r >> C) & 1) == CV)
+                pair2x2<false>(v[r], v[r | (1 << B)], m01, m00, m11, m10);
+            else
+                pair2x2<false>(v[r], v[r | (1 << B)], m00, m01, m10, m11);
+        }
+    } else if constexpr (B < W && C < W && T < W) {
+        const float2 m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
+        float2 x[1 << W];
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) x[r] = v[((r >> C) & 1) == CV ? (r ^ (1 << T)) : r];
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) {
+            if (r & (1 << B)) continue;
+            pair2x2<false>(x[r], x[r | (1 << B)], m00, m01, m10, m11);
+        }
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) v[r] = x[r];
+    }
+}
+
 // members exchanged across bit B (C < 0) or where window bit C equals CV: a
 // renaming of registers, no arithmetic, but moves where the cases rejoin
 template <int W, int B, int C, int CV>
@@ -316,6 +347,11 @@ __device__ __forceinline__ uint32_t insert_zeros_win(uint32_t g, const BOp &op) 
     case WC_D1CX + wc_opair(C, T) * 2 + 1: win_dense1_cx<W, T, C, T, 1>(v, m); break;               \
     case WC_D1CX + (12 + wc_opair(C, T)) * 2: win_dense1_cx<W, C, C, T, 0>(v, m); break;            \
     case WC_D1CX + (12 + wc_opair(C, T)) * 2 + 1: win_dense1_cx<W, C, C, T, 1>(v, m); break;
+#define SV_WC_CXD1(C, T)                                                                             \
+    case WC_CXD1 + wc_opair(C, T) * 2: win_cx_dense1<W, T, C, T, 0>(v, m); break;                   \
+    case WC_CXD1 + wc_opair(C, T) * 2 + 1: win_cx_dense1<W, T, C, T, 1>(v, m); break;               \
+    case WC_CXD1 + (12 + wc_opair(C, T)) * 2: win_cx_dense1<W, C, C, T, 0>(v, m); break;            \
+    case WC_CXD1 + (12 + wc_opair(C, T)) * 2 + 1: win_cx_dense1<W, C, C, T, 1>(v, m); break;
 #define SV_WC_CX(B, C)                                                            \
     case WC_CXSWAP + (4 * B + C) * 2: win_xswap<W, B, C, 0>(v); break;           \
     case WC_CXSWAP + (4 * B + C) * 2 + 1: win_xswap<W, B, C, 1>(v); break;
@@ -350,6 +386,8 @@ __device__ void op_window(float2 *tile, const BOp &op, const float2 *blk, int T)
                 SV_WC_CX(2, 0) SV_WC_CX(2, 1) SV_WC_CX(2, 3) SV_WC_CX(3, 0) SV_WC_CX(3, 1) SV_WC_CX(3, 2)
                 SV_WC_D1CX(0, 1) SV_WC_D1CX(0, 2) SV_WC_D1CX(0, 3) SV_WC_D1CX(1, 0) SV_WC_D1CX(1, 2) SV_WC_D1CX(1, 3)
                 SV_WC_D1CX(2, 0) SV_WC_D1CX(2, 1) SV_WC_D1CX(2, 3) SV_WC_D1CX(3, 0) SV_WC_D1CX(3, 1) SV_WC_D1CX(3, 2)
+                SV_WC_CXD1(0, 1) SV_WC_CXD1(0, 2) SV_WC_CXD1(0, 3) SV_WC_CXD1(1, 0) SV_WC_CXD1(1, 2) SV_WC_CXD1(1, 3)
+                SV_WC_CXD1(2, 0) SV_WC_CXD1(2, 1) SV_WC_CXD1(2, 3) SV_WC_CXD1(3, 0) SV_WC_CXD1(3, 1) SV_WC_CXD1(3, 2)
             default: {
                 const uint32_t hx = __float_as_uint(h0.x);
                 win_diag<W>(v, m, hx >> 24, (hx >> 8) & 0xff, (hx >> 16) & 0xff, cm, cv);
@@ -365,6 +403,7 @@ __device__ void op_window(float2 *tile, const BOp &op, const float2 *blk, int T)
 #undef SV_WC_PAIR
 #undef SV_WC_CX
 #undef SV_WC_D1CX
+#undef SV_WC_CXD1
 
 __device__ double block_sum(double v, double *red) {
 #pragma unroll

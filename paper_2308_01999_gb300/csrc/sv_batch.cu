@@ -73,7 +73,56 @@ bool gate_ok(const sv_gate_t &g, int n, int tile_qubits) {
 }
 
 // exact structure analysis of one (fused) gate -> at most one op
-bool classify(Gate g, std::vector<QOp> &out) {
+// A dense two-target gate M (bit j of its index on target t[j]) that is a
+// CNOT P between its targets (control bit c with value v, target bit 1 - c)
+// times a 2x2 gate K on one target alone, M = P K or M = K P: the factors in
+// the order they apply. Gate fusion (Sec. II-B) makes such blocks whenever a
+// CNOT meets a one-qubit gate on only one of its qubits; as one 4x4 product
+// they cost twice the arithmetic of K followed by an exchange. P is its own
+// inverse, so K = P M or M P, which must have the form K (x) I up to 1e-12.
+bool split_cx(const Gate &g, Gate &first, Gate &second) {
+    if (g.t.size() != 2) return false;
+    constexpr double kTol = 1e-12;
+    const std::vector<cd> &M = g.m;
+    for (int c = 0; c < 2; ++c)
+        for (int v = 0; v < 2; ++v) {
+            const int t = 1 - c;
+            auto pidx = [&](int i) { return ((i >> c) & 1) == v ? (i ^ (1 << t)) : i; };
+            for (int order = 0; order < 2; ++order) {
+                cd N[16];
+                for (int r = 0; r < 4; ++r)
+                    for (int q = 0; q < 4; ++q) N[r * 4 + q] = order == 0 ? M[pidx(r) * 4 + q] : M[r * 4 + pidx(q)];
+                for (int j = 0; j < 2; ++j) {           // K acts on target bit j
+                    const int o = 1 - j;
+                    cd B[4];
+                    bool ok = true;
+                    // rows in increasing order: a row with bit o set comes after its partner
+                    for (int r = 0; r < 4 && ok; ++r)
+                        for (int q = 0; q < 4 && ok; ++q) {
+                            const cd x = N[r * 4 + q];
+                            if (((r >> o) & 1) != ((q >> o) & 1)) {
+                                ok = std::abs(x) <= kTol;
+                            } else {
+                                cd &b = B[((r >> j) & 1) * 2 + ((q >> j) & 1)];
+                                if (((r >> o) & 1) == 0) b = x;
+                                else ok = std::abs(x - b) <= kTol;
+                            }
+                        }
+                    if (!ok) continue;
+                    Gate K{{g.t[j]}, g.c, g.cv, {B[0], B[1], B[2], B[3]}};
+                    Gate X{{g.t[t]}, g.c, g.cv, {cd(0), cd(1), cd(1), cd(0)}};
+                    X.c.push_back(g.t[c]);
+                    X.cv.push_back(v);
+                    first = order == 0 ? K : X;
+                    second = order == 0 ? X : K;
+                    return true;
+                }
+            }
+        }
+    return false;
+}
+
+bool classify(Gate g, std::vector<QOp> &out, bool split) {
     svc::simplify_controls(g);
     const int k = (int)g.t.size();
     QOp op;
@@ -95,6 +144,7 @@ bool classify(Gate g, std::vector<QOp> &out) {
         std::vector<cd> d;
         const int D = 1 << k;
         if (k > 4) return false;
+        Gate f1, f2;
         if (svc::as_permutation(g, perm, d)) {
             // source member l = perm[j] goes to destination j with factor d[j]
             op.kind = svk::BOP_PERM;
@@ -103,6 +153,8 @@ bool classify(Gate g, std::vector<QOp> &out) {
                 op.data[perm[j]] = d[j];
                 op.data[D + perm[j]] = cd((double)j, 0);
             }
+        } else if (split && split_cx(g, f1, f2)) {
+            return classify(f1, out, split) && classify(f2, out, split);
         } else {
             op.kind = svk::BOP_DENSE;
             op.data = g.m;
@@ -171,31 +223,54 @@ bool plain_cx(const QOp &qo) {
            qo.data[1] == cd(1, 0);
 }
 
-// Pairs each plain controlled exchange (CNOT, control value 0 or 1) with the
-// nearest earlier uncontrolled one-qubit dense op on one of its qubits, where
-// the ops between them leave that op's qubit alone: the dense op moves forward
-// to the exchange and writes its outputs straight into the exchanged
-// registers. Returns the window's items in a valid order, each {op, exchange
-// or -1}.
-std::vector<std::pair<int, int>> pair_exchanges(const std::vector<QOp> &qops, const std::vector<int> &idx) {
-    std::vector<std::pair<int, int>> it;
-    for (int i : idx) it.push_back({i, -1});
+// A window item: an op, optionally fused with a plain controlled exchange that
+// runs after it (or before it, cx_first).
+struct WItemOp {
+    int op, cx;
+    bool cx_first;
+};
+
+// Pairs each plain controlled exchange (CNOT, control value 0 or 1) with an
+// uncontrolled one-qubit dense op on one of its qubits: first the nearest
+// earlier one, where the ops between them leave that op's qubit alone (the
+// dense op moves forward to the exchange and writes its outputs straight into
+// the exchanged registers); else the nearest later one under the same
+// condition (the dense op moves back to the exchange and reads the exchanged
+// registers). Returns the window's items in a valid order.
+std::vector<WItemOp> pair_exchanges(const std::vector<QOp> &qops, const std::vector<int> &idx) {
+    std::vector<WItemOp> it;
+    for (int i : idx) it.push_back({i, -1, false});
+    auto mask_of = [&](const WItemOp &w) { return qops[w.op].qmask | (w.cx >= 0 ? qops[w.cx].qmask : 0); };
     for (size_t j = 0; j < it.size(); ++j) {
-        const QOp &cx = qops[it[j].first];
-        if (it[j].second >= 0 || !plain_cx(cx)) continue;
+        const QOp &cx = qops[it[j].op];
+        if (it[j].cx >= 0 || !plain_cx(cx)) continue;
+        bool paired = false;
         uint64_t between = 0;
         for (size_t i = j; i-- > 0;) {
-            const QOp &o = qops[it[i].first];
-            if (it[i].second < 0 && plain_dense1(o) && (o.qmask & cx.qmask)) {
+            const QOp &o = qops[it[i].op];
+            if (it[i].cx < 0 && plain_dense1(o) && (o.qmask & cx.qmask)) {
                 if ((between & o.qmask) == 0) {            // the dense op moves forward to the exchange
-                    it[j] = {it[i].first, it[j].first};
+                    it[j] = {it[i].op, it[j].op, false};
                     it.erase(it.begin() + (long)i);
                     --j;
+                    paired = true;
                 }
                 break;
             }
-            between |= o.qmask;
-            if (it[i].second >= 0) between |= qops[it[i].second].qmask;
+            between |= mask_of(it[i]);
+        }
+        if (paired) continue;
+        between = 0;
+        for (size_t i = j + 1; i < it.size(); ++i) {
+            const QOp &o = qops[it[i].op];
+            if (it[i].cx < 0 && plain_dense1(o) && (o.qmask & cx.qmask)) {
+                if ((between & o.qmask) == 0) {            // the dense op moves back to the exchange
+                    it[j] = {it[i].op, it[j].op, true};
+                    it.erase(it.begin() + (long)i);
+                }
+                break;
+            }
+            between |= mask_of(it[i]);
         }
     }
     return it;
@@ -205,7 +280,7 @@ std::vector<std::pair<int, int>> pair_exchanges(const std::vector<QOp> &qops, co
 // applied one after another to 2^|wq| amplitudes held in registers
 void emit_window(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vector<int> &idx_in, uint64_t wq,
                  uint64_t lm) {
-    const std::vector<std::pair<int, int>> items = pair_exchanges(qops, idx_in);
+    const std::vector<WItemOp> items = pair_exchanges(qops, idx_in);
     svk::BOp op{};
     op.kind = svk::BOP_WIN;
     op.k = (uint8_t)items.size();
@@ -224,7 +299,7 @@ void emit_window(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vecto
     const size_t hdr = b->pool.size();
     b->pool.resize(hdr + 2 * items.size());
     for (size_t s = 0; s < items.size(); ++s) {
-        const QOp &qo = qops[items[s].first];
+        const QOp &qo = qops[items[s].op];
         uint32_t cm = 0, cv = 0;
         for (size_t i = 0; i < qo.c.size(); ++i) {
             cm |= 1u << wbit(qo.c[i]);
@@ -254,10 +329,11 @@ void emit_window(sv_batch_ctx *b, const std::vector<QOp> &qops, const std::vecto
             for (int l = 0; l < 2; ++l) b->pool.push_back(make_float2((float)qo.data[l].real(), (float)qo.data[l].imag()));
         } else {
             kind = k == 1 ? svk::BSUB_DENSE1 : svk::BSUB_DENSE2;
-            if (items[s].second >= 0) {
-                const QOp &cx = qops[items[s].second];
+            if (items[s].cx >= 0) {
+                const QOp &cx = qops[items[s].cx];
                 const int c = wbit(cx.c[0]), t = wbit(cx.t[0]);
-                wc = svk::WC_D1CX + (uint32_t)(((b0 == t ? 0 : 12) + svk::wc_opair(c, t)) * 2 + (cx.cv[0] ? 1 : 0));
+                wc = (items[s].cx_first ? svk::WC_CXD1 : svk::WC_D1CX) +
+                     (uint32_t)(((b0 == t ? 0 : 12) + svk::wc_opair(c, t)) * 2 + (cx.cv[0] ? 1 : 0));
             } else if (k == 1)
                 wc = (cm ? svk::WC_DENSE1C : svk::WC_DENSE1) + b0;
             else
@@ -488,6 +564,10 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
         std::vector<svf::Item> fused;
         sv_status_t s = svf::fuse(gates + it.gate_begin, it.n_gates, n, fusion_width, fused, 0, keep_perm != 0);
         if (s != SV_OK) return s;
+        // split CNOT-times-one-qubit blocks only where register windows can
+        // take the two parts together: without windows each part is a pass
+        const int T = std::min(n, tile_qubits);
+        const bool split = std::min(window_qubits, T - 9) >= 2;
         std::vector<QOp> qops;
         for (const svf::Item &f : fused) {
             Gate g;
@@ -503,10 +583,9 @@ SV_API sv_status_t sv_batch_compile_ex(sv_batch_t b, const sv_batch_item_t *item
                 g.t = f.qubits;
                 g.m = f.m;
             }
-            if (!classify(g, qops)) return SV_ERR_NOT_SUPPORTED;
+            if (!classify(g, qops, split)) return SV_ERR_NOT_SUPPORTED;
         }
         // stages of at most T local qubits
-        const int T = std::min(n, tile_qubits);
         struct St { uint64_t q; std::vector<int> ops; };
         std::vector<St> sts;
         std::vector<int> last(n, -1);
@@ -594,6 +673,34 @@ SV_API sv_status_t sv_batch_info(sv_batch_t b, int *n_items, int *n_stages, int 
     if (n_ops) *n_ops = (int)b->ops.size();
     if (state_amps) *state_amps = b->state_amps;
     if (launches) *launches = b->launches;
+    return SV_OK;
+}
+
+SV_API sv_status_t sv_batch_program_stats(sv_batch_t b, uint64_t counts[SV_BATCH_STATS]) {
+    if (!b || !counts || !b->compiled) return SV_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < SV_BATCH_STATS; ++i) counts[i] = 0;
+    for (const svk::BOp &op : b->ops) {
+        if (op.kind != svk::BOP_WIN) {
+            ++counts[op.kind == svk::BOP_DENSE ? 0 : op.kind == svk::BOP_DIAG ? 1 : 2];
+            continue;
+        }
+        ++counts[3];
+        for (int s = 0; s < op.k; ++s) {
+            uint32_t hy;
+            std::memcpy(&hy, &b->pool[op.mat + 2 * s].y, 4);
+            const uint32_t wc = hy >> 16;
+            if (wc < svk::WC_DENSE2 || wc >= svk::WC_D1CX) {
+                ++counts[4];
+                if (wc >= svk::WC_D1CX) ++counts[5];
+            } else if (wc < svk::WC_SWAP1) {
+                ++counts[6];
+            } else if (wc < svk::WC_DIAG) {
+                ++counts[7];
+            } else {
+                ++counts[8];
+            }
+        }
+    }
     return SV_OK;
 }
 

@@ -123,6 +123,8 @@ enum BatchWinCase {
     WC_DIAG = 60,      // diagonal, run-time bits and control
     WC_D1CX = 64,      // + ((s ? 12 : 0) + wc_opair(c, t)) * 2 + v: 2x2 on bit t (s = 0) or c (s = 1),
                        //   then members exchanged across bit t where bit c == v
+    WC_CXD1 = 112,     // + ((s ? 12 : 0) + wc_opair(c, t)) * 2 + v: members exchanged across bit t where
+                       //   bit c == v, then a 2x2 on bit t (s = 0) or c (s = 1)
 };
 // index of the pair b0 < b1 < 4 among 01 02 03 12 13 23
 constexpr __host__ __device__ int wc_pair(int b0, int b1) { return b0 * (7 - b0) / 2 + (b1 - b0 - 1); }

@@ -40,7 +40,8 @@ EXPORTED = [
     "sv_copy_from_host", "sv_copy_to_host", "sv_apply_matrix", "sv_apply_fused", "sv_fuse_plan",
     "sv_expectation_pauli", "sv_measure_probs", "sv_collapse", "sv_measure", "sv_norm2",
     "sv_check_device_status", "sv_launch_count", "sv_status_string", "sv_expectation_pauli_noalloc",
-    "sv_batch_create", "sv_batch_destroy", "sv_batch_compile", "sv_batch_info", "sv_batch_launch",
+    "sv_batch_create", "sv_batch_destroy", "sv_batch_compile", "sv_batch_info", "sv_batch_program_stats",
+    "sv_batch_launch",
     "sv_batch_results", "sv_swap_index_bits", "sv_apply_pauli_rotation", "sv_sample",
     "sv_check_bounded_wait", "sv_apply_fused_ex", "sv_fuse_plan_ex", "sv_copy_from_host_async",
     "sv_copy_to_host_async", "sv_batch_compile_ex", "sv_set_state", "sv_pool_create", "sv_pool_destroy",
@@ -96,6 +97,7 @@ def lib():
             "sv_batch_compile": [_VP, _VP, C.c_int, _VP, C.c_int, _I, C.c_int],
             "sv_batch_compile_ex": [_VP, _VP, C.c_int, _VP, C.c_int, _I, _VP],
             "sv_batch_info": [_VP, _I, _I, _I, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
+            "sv_batch_program_stats": [_VP, C.POINTER(C.c_uint64)],
             "sv_batch_launch": [_VP, C.c_int, _VP, C.c_int],
             "sv_batch_results": [_VP, _D, C.c_int],
             "sv_swap_index_bits": [_VP, _I, C.c_int],
@@ -453,6 +455,7 @@ class StateVector:
 
 SV_BATCH_KEEP_STATES = 1
 SV_BATCH_CHECK_WAIT = 2
+SV_BATCH_STATS = 9
 SV_BATCH_MAX_QUBITS = 26
 SV_BATCH_TILE_QUBITS = 14     # largest (and default) tile: local qubits of one pass
 GATE_DTYPE = np.dtype([("n_targets", "<i4"), ("targets", "<i4", (SV_MAX_TARGETS,)), ("n_controls", "<i4"),
@@ -536,6 +539,17 @@ def sv_batch_info(b: int) -> dict:
            "sv_batch_info")
     return {"items": ni.value, "stages": ns.value, "ops": no.value, "state_amps": amps.value,
             "launches": launches.value}
+
+
+BATCH_STATS = ("dense_ops", "diagonal_ops", "permutation_ops", "windows", "win_2x2", "win_2x2_with_exchange",
+               "win_4x4", "win_exchanges", "win_diagonals")
+
+
+def sv_batch_program_stats(b: int) -> dict:
+    """What the compiled program does, by op and window sub-op kind."""
+    out = (C.c_uint64 * len(BATCH_STATS))()
+    _check(lib().sv_batch_program_stats(_VP(b), out), "sv_batch_program_stats")
+    return {k: int(v) for k, v in zip(BATCH_STATS, out)}
 
 
 def sv_batch_launch(b: int, d_states_ptr: int, keep_states: bool = False, dtype: int = SV_C64, flags: int = 0):
@@ -632,6 +646,9 @@ class Batch:
 
     def info(self):
         return sv_batch_info(self.handle)
+
+    def program_stats(self):
+        return sv_batch_program_stats(self.handle)
 
     def launch(self, d_states, keep_states: bool = False, flags: int = 0):
         """d_states: a complex64 CUDA tensor of at least `state_amps` elements, or

@@ -134,10 +134,11 @@ def test_tile_size_option_on_host(svmod):
 
 
 def test_keep_permutations_rule_on_host(svmod):
-    """With keep_permutations, a fused block that holds a CNOT, X or other
-    permutation takes no dense gate: a ladder of CNOTs between layers of Haar
-    gates then fuses to more ops, dense ones only where dense gates meet, and
-    an option value other than 0 or 1 is rejected."""
+    """With keep_permutations, a fused block that starts with a CNOT, X or
+    other permutation takes no dense gate: CNOTs on disjoint pairs, each
+    followed by Haar gates on both of its qubits, fuse to one dense block per
+    pair without the rule and to a permutation block plus a dense block per
+    pair with it; an option value other than 0 or 1 is rejected."""
     import ctypes as C
     sv = svmod
     rng = gen.rng_for(8)
@@ -145,8 +146,8 @@ def test_keep_permutations_rule_on_host(svmod):
     n = 12
     gates = []
     for _ in range(4):
+        gates += [gen.Gate((q + 1,), x, (q,), (1,)) for q in range(0, n, 2)]
         gates += [gen.Gate((q,), gen.haar_su2(rng)) for q in range(n)]
-        gates += [gen.Gate((q + 1,), x, (q,), (1,)) for q in range(n - 1)]
     prog = [(n, gates, np.zeros((0, n)))]
     ops = {}
     for keep in (False, True):
@@ -154,7 +155,7 @@ def test_keep_permutations_rule_on_host(svmod):
         ops[keep] = b.compile(prog, 2, 0, keep)["ops"]
         assert b.choice == (2, 0, int(keep), 14)
         b.close()
-    assert ops[True] > ops[False]
+    assert ops[False] == n // 2 and ops[True] == n
     packed = sv.pack_batch(prog)
     h = C.c_void_p()
     assert sv.lib().sv_batch_create(None, C.byref(h)) == 0
@@ -319,6 +320,76 @@ def test_register_window_exchange_cases(svmod, window):
     want = np.array([orc.expect_pauli(ref, p, list(range(n))).real for p in paulis])
     assert np.all(np.abs(res - want) <= 1e-6 * np.maximum(1, np.abs(want)))
     b.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("window", [4, 3, 0])
+def test_register_window_exchange_first_cases(svmod, window):
+    """CNOTs fused with the one-qubit product after them (the product moves
+    back to the exchange and reads the exchanged registers), where a CZ on the
+    same qubits stops a fold with the product before them: the product on the
+    exchange's target and on its control, control values 1 and 0, and a
+    product that moves back past an op on another qubit; windows of 4 and 3
+    qubits and none. Amplitudes and expectations against the oracle."""
+    import torch
+    sv = svmod
+    n = 13
+    rng = gen.rng_for(405)
+    x = np.array([[0, 1], [1, 0]], dtype=complex)
+    h = lambda q: gen.Gate((q,), gen.haar_su2(rng))         # noqa: E731
+    g = [h(q) for q in range(n)]
+    g += [gen.cz(0, 1), gen.cnot(0, 1), h(1)]                      # product on the target, value 1
+    g += [gen.cz(2, 3), gen.Gate((3,), x, (2,), (0,)), h(2)]       # product on the control, value 0
+    g += [gen.cz(0, 3), gen.cnot(3, 0), h(1), h(3)]                # on the control, past an op on qubit 1
+    g += [gen.cz(1, 2), gen.Gate((1,), x, (2,), (0,)), h(1)]       # on the target, value 0
+    g += [gen.cz(0, 2), gen.cnot(2, 0), h(2)]                      # on the control, value 1
+    g += [h(q) for q in range(4)]
+    paulis, _ = gen.random_pauli_strings(n, 4, rng)
+    for width in (1, 2):
+        b = sv.Batch(torch.cuda.current_stream())
+        b.compile([(n, g, paulis)], fusion_width=width, window_qubits=window)
+        buf = torch.zeros(b.state_amps, dtype=torch.complex64, device="cuda")
+        b.launch(buf, keep_states=True)
+        res = b.results()[0]
+        ref = orc.run_circuit(g, n)
+        amp = buf.cpu().numpy()[:1 << n].astype(np.complex128)
+        assert np.max(np.abs(amp - ref)) <= 1e-5, (width, window)
+        want = np.array([orc.expect_pauli(ref, p, list(range(n))).real for p in paulis])
+        assert np.all(np.abs(res - want) <= 1e-6 * np.maximum(1, np.abs(want))), (width, window)
+        b.close()
+
+
+def test_cnot_times_one_qubit_blocks_are_split_on_host(svmod):
+    """A fused two-qubit block that is a CNOT times a one-qubit gate on one of
+    its qubits (either order) is compiled as the 2x2 product fused with the
+    exchange inside a register window, not as one 4x4 product; a block with
+    one-qubit gates on both qubits stays a 4x4 product, and without windows
+    nothing is split (each part would be a pass of its own)."""
+    sv = svmod
+    rng = gen.rng_for(406)
+    n = 14
+    h = lambda q: gen.Gate((q,), gen.haar_su2(rng))         # noqa: E731
+    cases = {
+        "gate then cnot, gate on control": [h(0), gen.cnot(0, 1)],
+        "gate then cnot, gate on target": [h(1), gen.cnot(0, 1)],
+        "cnot then gate on control": [gen.cnot(0, 1), h(0)],
+        "cnot then gate on target, control value 0": [gen.Gate((1,), np.array([[0, 1], [1, 0]], complex), (0,), (0,)),
+                                                       h(1)],
+        "gates on both qubits": [h(0), h(1), gen.cnot(0, 1)],
+    }
+    for name, gates in cases.items():
+        both = name == "gates on both qubits"
+        b = sv.Batch()
+        b.compile([(n, gates, np.zeros((0, n)))], 2, 4)
+        st = b.program_stats()
+        if both:          # one 4x4 product (a window of one op is emitted as the op)
+            assert st["win_4x4"] + st["dense_ops"] == 1 and st["win_2x2"] == 0, (name, st)
+        else:
+            assert st["windows"] == 1 and st["dense_ops"] == 0 and st["win_4x4"] == 0, (name, st)
+            assert st["win_2x2"] == st["win_2x2_with_exchange"] == 1, (name, st)
+        assert b.compile([(n, gates, np.zeros((0, n)))], 2, 0)["ops"] == 1      # no windows: no split
+        assert b.program_stats()["dense_ops"] == 1
+        b.close()
 
 
 @pytest.mark.gpu
