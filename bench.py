@@ -189,6 +189,14 @@ def cpu_baseline(gates, budget_s: float = 12.0):
                       f"({cores} OpenMP threads), {dt:.1f} s; GB/s counts the complex64 workload's bytes"}
 
 
+def line_config(world: int, n_gates: int, nbytes: float) -> dict:
+    """The workload's `config` object, the same on both arms of the bench."""
+    return {"workload": workload_name(), "n_qubits": N_QUBITS, "depth": DEPTH, "gates_per_step": n_gates,
+            "state_bytes": AMP_BYTES << N_QUBITS, "bytes_per_step": nbytes,
+            "l2": f"no flush: the {(8 << N_QUBITS) / 2**30:g} GiB state exceeds the 129 MB L2",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     """The oracle as it stands, timed on the host cores on the same workload,
     each step a bounded sample (a fixed slice of the circuit's gates)."""
@@ -196,7 +204,8 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import oracle as orc
-    gates, _, _ = workload()
+    gates, paulis, _ = workload()
+    config = line_config(world, len(gates), step_bytes(gates, paulis))
     cores = orc.set_threads(0)
     psi = orc.zero_state(N_QUBITS)
     per_step = 4
@@ -218,13 +227,14 @@ def run_reference(args):
     moved = sum(one_step() for _ in range(args.steps))
     dt = time.perf_counter() - t0
     value = moved / dt / 1e9
-    sample = (f"{per_step} consecutive gates per step of the 28-qubit circuit, complex128 oracle, "
-              f"{cores} OpenMP threads; GB/s counts the complex64 workload's bytes")
+    sample = (f"each step {per_step} consecutive gates of the {N_QUBITS}-qubit circuit's {len(gates)} (the "
+              f"config's step), complex128 oracle, {cores} OpenMP threads; GB/s counts the complex64 "
+              "workload's bytes of the gates applied")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(), "n_qubits": N_QUBITS},
+        "data": "synthetic", "config": config,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -367,10 +377,7 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(), "n_qubits": N_QUBITS, "depth": DEPTH, "gates_per_step": n_gates,
-                   "state_bytes": AMP_BYTES << N_QUBITS, "bytes_per_step": nbytes,
-                   "l2": f"no flush: the {(8 << N_QUBITS) / 2**30:g} GiB state exceeds the 129 MB L2",
-                   "parallelism": f"replicas x{world}"},
+        "config": line_config(world, n_gates, nbytes),
         "gates_per_s": round(world * n_gates / (gates_ms * 1e-3), 1),
         "gate_time_ms_per_step": round(gates_ms, 3),
         "roofline": {"bound": "hbm", "kernel": "k_dense (1-qubit dense, SU(2))", "achieved": round(achieved, 1),
