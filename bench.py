@@ -400,10 +400,11 @@ def run_ours(args):
     del s, psi
     torch.cuda.empty_cache()
     if world == 1 and not args.main_only:
-        # the 30-qubit size of the bandwidth target and the other two parts of
-        # the headline metric, on the same GPU after the 28-qubit step (rank 0
-        # at N = 1 only, like the CPU baseline)
+        # the 30-qubit size of the bandwidth target, the 32-qubit fused circuit
+        # and the other two parts of the headline metric, on the same GPU after
+        # the 28-qubit step (rank 0 at N = 1 only, like the CPU baseline)
         line["n30"] = n30_section(args)
+        line["fused32"] = fused32_section(args)
         line["batch"] = batch_section(args)
         line["serve"] = serve_section(args)
     print(json.dumps(line))
@@ -534,6 +535,66 @@ def run_fused(args):
         s.close()
     out["peaks"] = {"hbm_gbs": peak_hbm, "bf16_tflops": bf16_peak, "tf32_tflops_from_nominal_ratio": round(tf32_peak, 1)}
     print(json.dumps(out))
+
+
+def fused32_section(args, n: int = 32) -> dict:
+    """The 32-qubit fused brick wall (40 layers of Haar SU(2) + CZ wall, 1900
+    gates, 32 GiB complex64 state) in the default line: the unfused complex64
+    run (one gate per launch), then one sv_apply_fused call at width 6 in TF32
+    and one in split BF16 (host fusion, relabelling choice and every block,
+    5-6-qubit blocks on the tensor cores), each timed with CUDA events on the
+    handle's stream. Errors of the fused runs are measured against the
+    unfused complex64 state (whose own distance to a complex128 run of the
+    circuit is ~2e-6, far below the tensor-core errors)."""
+    import torch
+
+    from paper_2308_01999_gb300 import sv
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.empty_cache()
+    gates = gen.circuit_config2(n, 40, seed=2)
+    stream = torch.cuda.Stream(dev)
+    out = {"workload": f"{n}-qubit brick wall, 40 layers of Haar SU(2) + CZ, {len(gates)} gates, complex64 "
+                       "(32 GiB); fused width 6 on the tensor cores vs unfused"}
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    with torch.cuda.stream(stream):
+        ref = torch.empty(1 << n, dtype=torch.complex64, device=dev)
+        r = sv.StateVector(ref, stream)
+        r.set_basis_state(0)
+        out["unfused_c64_s"] = round(timed(lambda: r.apply_circuit(gates)), 3)
+        ref_z = r.expectation_z_all()
+        r.close()
+        psi = torch.empty(1 << n, dtype=torch.complex64, device=dev)
+        s = sv.StateVector(psi, stream)
+        for name, prec in (("tf32", sv.SV_PREC_TF32), ("bf16", sv.SV_PREC_SPLIT_BF16)):
+            s.set_basis_state(0)
+            torch.cuda.synchronize()
+            sec = timed(lambda: s.apply_fused(gates, 6, prec))
+            s.check()
+            num = den = mx = 0.0
+            chunk = 1 << 28
+            for a in range(0, 1 << n, chunk):
+                d = psi[a:a + chunk] - ref[a:a + chunk]
+                num += float(torch.sum(torch.abs(d).double() ** 2))
+                den += float(torch.sum(torch.abs(ref[a:a + chunk]).double() ** 2))
+                mx = max(mx, float(torch.max(torch.abs(d))))
+            z = s.expectation_z_all()
+            out[name] = {"one_call_s": round(sec, 3), "speedup_vs_unfused": round(out["unfused_c64_s"] / sec, 2),
+                         "rel_l2_vs_unfused_c64": num ** 0.5 / den ** 0.5, "max_abs_vs_unfused_c64": mx,
+                         "max_abs_z_vs_unfused_c64": float(np.max(np.abs(z - ref_z)))}
+        s.close()
+    del psi, ref
+    torch.cuda.empty_cache()
+    out["blocks"] = len(sv.sv_fuse_plan(gates, n, 6))
+    return out
 
 
 def n30_section(args, n: int = 30) -> dict:
@@ -1008,6 +1069,10 @@ def run_n30(args):
     print(json.dumps(n30_section(args)))
 
 
+def run_fused_brief(args):
+    print(json.dumps(fused32_section(args)))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1017,7 +1082,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--qubits", type=int, default=28,
                     help="state size; 28 is the benchmark workload, smaller sizes are for profiling captures")
-    ap.add_argument("--workload", choices=("circuit28", "fused32", "batch", "serve", "n30", "cpu-plan", "gates"),
+    ap.add_argument("--workload", choices=("circuit28", "fused32", "fused32-brief", "batch", "serve", "n30",
+                                           "cpu-plan", "gates"),
                     default="circuit28",
                     help="fused32: the 32-qubit fused brick-wall study (tensor cores, errors vs complex128)")
     ap.add_argument("--fused-qubits", type=int, default=32)
@@ -1051,6 +1117,8 @@ def main():
         run_serve(args)
     elif args.workload == "n30":
         run_n30(args)
+    elif args.workload == "fused32-brief":
+        run_fused_brief(args)
     elif args.workload == "cpu-plan":
         run_cpu_plan(args)
     elif args.workload == "gates":
