@@ -4,9 +4,11 @@
 //
 // Three kernel families, all in place:
 //   k_dense      dense 2^k x 2^k product per group, k <= 4, group data in registers;
+//   k_dense5     dense product for k = 5 in complex64, one group per thread in
+//                registers, the matrix broadcast from shared memory;
 //   k_dense_smem dense product for any k <= 6, a tile of groups staged in shared memory
-//                (for k = 5, 6 the work is ALU-bound on CUDA cores; the tensor-core
-//                path in k_tc.cu is the fast one);
+//                (k = 6, and k = 5 in complex128; for k = 5, 6 the work is ALU-bound
+//                on CUDA cores; the tensor-core path in k_tc.cu is the fast one);
 //   k_diag       diagonal matrix on the amplitudes where the controls hold;
 //   k_perm       generalized permutation matrix (one nonzero per row/column).
 //
@@ -291,6 +293,68 @@ k_dense_smem(typename CT<R>::T *__restrict__ sv, uint64_t n_groups, GroupGeom G,
 }
 
 // ---------------------------------------------------------------------------
+// dense k = 5, complex64: compute-bound on CUDA cores (128 FMAs per amplitude
+// against 16 bytes moved, above the FP32 : HBM ratio). Each thread holds one
+// group's 32 amplitudes in registers and forms its outputs 8 at a time from
+// the matrix in shared memory (16-byte broadcast loads, two entries of a row
+// per load: one load per 8 FMAs), writing each output straight back to its
+// amplitude -- all inputs are in registers by then and no other thread
+// touches the group. With qubit 0 a target (PAIR0) members 2m and 2m + 1 are
+// adjacent amplitudes and move as one 16-byte access.
+// ---------------------------------------------------------------------------
+template <bool PAIR0>
+__global__ void __launch_bounds__(kThreads, 2)
+k_dense5(float2 *__restrict__ sv, uint64_t n_groups, GroupGeom G, Offs<5> O, const float2 *__restrict__ Mg) {
+    __shared__ __align__(16) float2 Ms[32 * 32];
+    for (int i = threadIdx.x; i < 32 * 32; i += kThreads) Ms[i] = Mg[i];
+    __syncthreads();
+    const float4 *M4 = reinterpret_cast<const float4 *>(Ms);
+    for (uint64_t g = (uint64_t)blockIdx.x * kThreads + threadIdx.x; g < n_groups;
+         g += (uint64_t)gridDim.x * kThreads) {
+        const uint64_t base = insert_zeros(g, G);
+        float2 x[32];
+        if constexpr (PAIR0) {
+#pragma unroll
+            for (int l = 0; l < 32; l += 2) {
+                const float4 q = ld16(sv + base + O.o[l]);
+                x[l] = make_float2(q.x, q.y);
+                x[l + 1] = make_float2(q.z, q.w);
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l < 32; ++l) x[l] = sv[base + O.o[l]];
+        }
+        // the stores recompute their addresses from an opaque copy of the base,
+        // so the 32 load addresses (64 registers) are not kept alive for them
+        float2 *ps;
+        asm volatile("mov.b64 %0, %1;" : "=l"(ps) : "l"(sv + base));
+#pragma unroll
+        for (int j0 = 0; j0 < 32; j0 += 8) {
+            float2 acc[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) acc[jj] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int l = 0; l < 32; l += 2) {
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const float4 m2 = M4[((j0 + jj) * 32 + l) >> 1];
+                    cmad(acc[jj], make_float2(m2.x, m2.y), x[l]);
+                    cmad(acc[jj], make_float2(m2.z, m2.w), x[l + 1]);
+                }
+            }
+            if constexpr (PAIR0) {
+#pragma unroll
+                for (int jj = 0; jj < 8; jj += 2)
+                    st16(ps + O.o[j0 + jj], make_float4(acc[jj].x, acc[jj].y, acc[jj + 1].x, acc[jj + 1].y));
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) ps[O.o[j0 + jj]] = acc[jj];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // diagonal on targets where the controls hold (k = 0 is a phase on a subspace)
 // ---------------------------------------------------------------------------
 template <typename R> struct DiagP {
@@ -550,6 +614,36 @@ cudaError_t dense_smem(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, 
     return cudaGetLastError();
 }
 
+cudaError_t dense5_c64(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, const double *mat,
+                       void *d_mat) {
+    Offs<5> O;
+    for (int j = 0; j < 32; ++j) {
+        uint64_t o = 0;
+        for (int t = 0; t < 5; ++t)
+            if ((j >> t) & 1) o |= 1ull << tpos[t];
+        O.o[j] = o;
+    }
+    std::vector<float2> hm(32 * 32);
+    for (int i = 0; i < 32 * 32; ++i) hm[i] = to_c<float2>(mat + 2 * i);
+    cudaError_t e = cudaMemcpyAsync(d_mat, hm.data(), sizeof(float2) * 32 * 32, cudaMemcpyHostToDevice, L.stream);
+    if (e != cudaSuccess) return e;
+    // qubit 0 a target: tpos[0] == 0 (targets ascending), and the base of every
+    // group is even, so member pairs are 16-byte aligned
+    const bool pair0 = tpos[0] == 0;
+    auto kern = pair0 ? k_dense5<true> : k_dense5<false>;
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    const uint64_t n_groups = 1ull << (n - G.ns);
+    uint64_t grid = (uint64_t)L.num_sms * (per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (n_groups + kThreads - 1) / kThreads;
+    if (grid > need) grid = need;
+    kern<<<(unsigned)grid, kThreads, 0, L.stream>>>(reinterpret_cast<float2 *>(sv), n_groups, G, O,
+                                                    reinterpret_cast<const float2 *>(d_mat));
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t dense_any(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, int k,
                       const double *mat, void *d_mat) {
@@ -558,7 +652,9 @@ cudaError_t dense_any(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, c
     case 2: return dense_reg<R, 2>(L, sv, n, G, tpos, mat);
     case 3: return dense_reg<R, 3>(L, sv, n, G, tpos, mat);
     case 4: return dense_reg<R, 4>(L, sv, n, G, tpos, mat);
-    case 5: return dense_smem<R, 5>(L, sv, n, G, tpos, mat, d_mat);
+    case 5:
+        if constexpr (std::is_same<R, float>::value) return dense5_c64(L, sv, n, G, tpos, mat, d_mat);
+        else return dense_smem<R, 5>(L, sv, n, G, tpos, mat, d_mat);
     case 6: return dense_smem<R, 6>(L, sv, n, G, tpos, mat, d_mat);
     default: return cudaErrorInvalidValue;
     }
