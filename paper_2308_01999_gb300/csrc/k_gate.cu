@@ -355,6 +355,76 @@ k_dense5(float2 *__restrict__ sv, uint64_t n_groups, GroupGeom G, Offs<5> O, con
 }
 
 // ---------------------------------------------------------------------------
+// dense k = 6, complex64: as k_dense5, but a group's 64 amplitudes are split
+// over the two lanes of a pair (h = lane & 1 holds the members whose top bit is
+// h). Each lane forms partial sums of 8 outputs at a time over its 32 inputs,
+// takes its partner's partials with one shuffle per value (the sum a + b is the
+// same in both lanes) and stores half of them. The host uses it only when the
+// group count is a multiple of 16, so every warp's pairs enter and leave the
+// grid-stride loop together and the shuffles see the whole warp.
+// ---------------------------------------------------------------------------
+template <bool PAIR0>
+__global__ void __launch_bounds__(kThreads, 2)
+k_dense6(float2 *__restrict__ sv, uint64_t n_groups, GroupGeom G, Offs<6> O, const float2 *__restrict__ Mg) {
+    __shared__ __align__(16) float2 Ms[64 * 64];
+    for (int i = threadIdx.x; i < 64 * 64; i += kThreads) Ms[i] = Mg[i];
+    __syncthreads();
+    const int h = threadIdx.x & 1;
+    const float4 *M4 = reinterpret_cast<const float4 *>(Ms) + h * 16;   // row j: M4[j * 32 + i / 2]
+    for (uint64_t g = ((uint64_t)blockIdx.x * kThreads + threadIdx.x) >> 1; g < n_groups;
+         g += ((uint64_t)gridDim.x * kThreads) >> 1) {
+        const uint64_t base = insert_zeros(g, G);
+        float2 x[32];
+        if constexpr (PAIR0) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+                const float4 q = ld16(sv + base + O.o[32 * h + i]);
+                x[i] = make_float2(q.x, q.y);
+                x[i + 1] = make_float2(q.z, q.w);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = sv[base + O.o[32 * h + i]];
+        }
+        float2 *ps;
+        asm volatile("mov.b64 %0, %1;" : "=l"(ps) : "l"(sv + base));
+#pragma unroll 1
+        for (int j0 = 0; j0 < 64; j0 += 8) {
+            float2 acc[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) acc[jj] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const float4 m2 = M4[(j0 + jj) * 32 + (i >> 1)];
+                    cmad(acc[jj], make_float2(m2.x, m2.y), x[i]);
+                    cmad(acc[jj], make_float2(m2.z, m2.w), x[i + 1]);
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                acc[jj].x += __shfl_xor_sync(0xffffffffu, acc[jj].x, 1);
+                acc[jj].y += __shfl_xor_sync(0xffffffffu, acc[jj].y, 1);
+            }
+            // lane h stores outputs j0 + 4h .. j0 + 4h + 3 (selected, not indexed,
+            // so that acc stays in registers)
+            float2 mine[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) mine[p] = h ? acc[4 + p] : acc[p];
+            if constexpr (PAIR0) {
+#pragma unroll
+                for (int p = 0; p < 4; p += 2)
+                    st16(ps + O.o[j0 + 4 * h + p], make_float4(mine[p].x, mine[p].y, mine[p + 1].x, mine[p + 1].y));
+            } else {
+#pragma unroll
+                for (int p = 0; p < 4; ++p) ps[O.o[j0 + 4 * h + p]] = mine[p];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // diagonal on targets where the controls hold (k = 0 is a phase on a subspace)
 // ---------------------------------------------------------------------------
 template <typename R> struct DiagP {
@@ -644,6 +714,34 @@ cudaError_t dense5_c64(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, 
     return cudaGetLastError();
 }
 
+cudaError_t dense6_c64(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, const double *mat,
+                       void *d_mat) {
+    Offs<6> O;
+    for (int j = 0; j < 64; ++j) {
+        uint64_t o = 0;
+        for (int t = 0; t < 6; ++t)
+            if ((j >> t) & 1) o |= 1ull << tpos[t];
+        O.o[j] = o;
+    }
+    std::vector<float2> hm(64 * 64);
+    for (int i = 0; i < 64 * 64; ++i) hm[i] = to_c<float2>(mat + 2 * i);
+    cudaError_t e = cudaMemcpyAsync(d_mat, hm.data(), sizeof(float2) * 64 * 64, cudaMemcpyHostToDevice, L.stream);
+    if (e != cudaSuccess) return e;
+    const bool pair0 = tpos[0] == 0;
+    auto kern = pair0 ? k_dense6<true> : k_dense6<false>;
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    const uint64_t n_groups = 1ull << (n - G.ns);
+    uint64_t grid = (uint64_t)L.num_sms * (per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (2 * n_groups + kThreads - 1) / kThreads;
+    if (grid > need) grid = need;
+    kern<<<(unsigned)grid, kThreads, 0, L.stream>>>(reinterpret_cast<float2 *>(sv), n_groups, G, O,
+                                                    reinterpret_cast<const float2 *>(d_mat));
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t dense_any(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, int k,
                       const double *mat, void *d_mat) {
@@ -655,7 +753,11 @@ cudaError_t dense_any(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, c
     case 5:
         if constexpr (std::is_same<R, float>::value) return dense5_c64(L, sv, n, G, tpos, mat, d_mat);
         else return dense_smem<R, 5>(L, sv, n, G, tpos, mat, d_mat);
-    case 6: return dense_smem<R, 6>(L, sv, n, G, tpos, mat, d_mat);
+    case 6:
+        // pairs of lanes per group: whole warps need a group count divisible by 16
+        if constexpr (std::is_same<R, float>::value)
+            if (n - G.ns >= 4) return dense6_c64(L, sv, n, G, tpos, mat, d_mat);
+        return dense_smem<R, 6>(L, sv, n, G, tpos, mat, d_mat);
     default: return cudaErrorInvalidValue;
     }
 }
