@@ -6,9 +6,11 @@
 //   k_dense      dense 2^k x 2^k product per group, k <= 4, group data in registers;
 //   k_dense5     dense product for k = 5 in complex64, one group per thread in
 //                registers, the matrix broadcast from shared memory;
+//   k_dense6     the same for k = 6, a group over a pair of lanes;
 //   k_dense_smem dense product for any k <= 6, a tile of groups staged in shared memory
-//                (k = 6, and k = 5 in complex128; for k = 5, 6 the work is ALU-bound
-//                on CUDA cores; the tensor-core path in k_tc.cu is the fast one);
+//                (complex128, and states of fewer than 16 groups; for k = 5, 6 the work
+//                is ALU-bound on CUDA cores; the tensor-core path in k_tc.cu is the
+//                fast one);
 //   k_diag       diagonal matrix on the amplitudes where the controls hold;
 //   k_perm       generalized permutation matrix (one nonzero per row/column).
 //
