@@ -597,6 +597,58 @@ def fused32_section(args, n: int = 32) -> dict:
     return out
 
 
+def run_e1(args):
+    """Gate-application bandwidth by number of targets (the paper's Sec. II-B
+    experiment): for k = 1..6, `--e1-sets` random target sets (sorted, seeded)
+    with a random dense 2^k x 2^k matrix each, one sv_apply_matrix launch per
+    set on a 33-qubit complex64 state (64 GiB) and `--e1-sets-c128` sets on a
+    32-qubit complex128 state (64 GiB), each launch timed with CUDA events on
+    the handle's stream (the state is 500 times L2, so no launch finds its
+    input in cache). Algorithmic bytes per launch: one read and one write of
+    the state. Per k: median, 10th/90th percentile, min and max GB/s, and the
+    median as a fraction of the measured copy peak."""
+    import torch
+
+    from paper_2308_01999_gb300 import sv
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    peak, kind = load_peaks()
+    out = {"workload": "random dense k-qubit gates, k = 1..6, one launch each", "peak_gbs": peak, "peak_kind": kind}
+    for name, n, dtype, sets in (("c64_33q", 33, torch.complex64, args.e1_sets),
+                                 ("c128_32q", 32, torch.complex128, args.e1_sets_c128)):
+        rng = gen.rng_for(2308 + n)
+        nbytes = 2 * (1 << n) * (8 if dtype == torch.complex64 else 16)
+        rec = {}
+        with torch.cuda.stream(stream):
+            psi = torch.empty(1 << n, dtype=dtype, device=dev)
+            s = sv.StateVector(psi, stream)
+            s.set_basis_state(0)
+            for k in range(1, 7):
+                cases = [(sorted(int(q) for q in rng.choice(n, k, replace=False)), gen.random_gate_dense(rng, k))
+                         for _ in range(sets)]
+                s.apply(cases[0][0], cases[0][1])          # first launch of this width: set-up
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in cases]
+                for (t, m), (a, b) in zip(cases, ev):
+                    a.record(stream)
+                    s.apply(t, m)
+                    b.record(stream)
+                torch.cuda.synchronize()
+                gbs = np.array([nbytes / (a.elapsed_time(b) * 1e-3) / 1e9 for a, b in ev])
+                rec[str(k)] = {"sets": sets, "median_gbs": round(float(np.median(gbs)), 1),
+                               "p10_gbs": round(float(np.percentile(gbs, 10)), 1),
+                               "p90_gbs": round(float(np.percentile(gbs, 90)), 1),
+                               "min_gbs": round(float(gbs.min()), 1), "max_gbs": round(float(gbs.max()), 1),
+                               "median_frac_of_peak": round(float(np.median(gbs)) / peak, 4)}
+                print(json.dumps({name: {str(k): rec[str(k)]}}), file=sys.stderr, flush=True)
+            rec["norm_minus_1"] = float(s.norm2() - 1.0)
+            s.close()
+        del psi
+        torch.cuda.empty_cache()
+        out[name] = rec
+    print(json.dumps(out))
+
+
 def n30_section(args, n: int = 30) -> dict:
     """The size of the >= 80 %-of-HBM target: one dense one-qubit SU(2) gate
     per launch on every target qubit of a 30-qubit complex64 state (8 GiB,
@@ -1083,7 +1135,7 @@ def main():
     ap.add_argument("--qubits", type=int, default=28,
                     help="state size; 28 is the benchmark workload, smaller sizes are for profiling captures")
     ap.add_argument("--workload", choices=("circuit28", "fused32", "fused32-brief", "batch", "serve", "n30",
-                                           "cpu-plan", "gates"),
+                                           "e1", "cpu-plan", "gates"),
                     default="circuit28",
                     help="fused32: the 32-qubit fused brick-wall study (tensor cores, errors vs complex128)")
     ap.add_argument("--fused-qubits", type=int, default=32)
@@ -1095,6 +1147,8 @@ def main():
     ap.add_argument("--batch-widths", default="", help="batch: 'fusion,window[,keep_permutations[,tile_qubits]]' instead of the autotuner")
     ap.add_argument("--gate-cases", default=GATE_CASES, help="gates: 'k:t0,t1,..' cases, space separated")
     ap.add_argument("--gate-reps", type=int, default=5, help="gates: timed launches per case")
+    ap.add_argument("--e1-sets", type=int, default=100, help="e1: random target sets per width, complex64")
+    ap.add_argument("--e1-sets-c128", type=int, default=20, help="e1: random target sets per width, complex128")
     ap.add_argument("--main-only", action="store_true",
                     help="only the 28-qubit line, without its batch and serve sections")
     ap.add_argument("--serve-requests", type=int, default=120, help="serve: requests of the offered-rate trace")
@@ -1117,6 +1171,8 @@ def main():
         run_serve(args)
     elif args.workload == "n30":
         run_n30(args)
+    elif args.workload == "e1":
+        run_e1(args)
     elif args.workload == "fused32-brief":
         run_fused_brief(args)
     elif args.workload == "cpu-plan":
