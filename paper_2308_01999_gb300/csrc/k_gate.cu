@@ -113,6 +113,40 @@ k_dense(typename CT<R>::T *__restrict__ sv, uint64_t n_units, GroupGeom G, Offs<
             }
         }
     }
+    if constexpr (MODE == T0 && K >= 3 && U > 1) {
+        // the thread's U groups side by side in the innermost loop, as PAIR mode
+        // does with its two: each matrix entry feeds U products (same sums in the
+        // same order per group); a group past the end computes on zeros, unstored
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (u0 + (uint64_t)u * kThreads >= n_units)
+#pragma unroll
+                for (int l = 0; l < D; ++l) v[u][l][0] = C{0, 0};
+#pragma unroll
+        for (int j0 = 0; j0 < D; j0 += 2) {
+            C w[2][U];
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                C acc[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc[u] = C{0, 0};
+#pragma unroll
+                for (int l = 0; l < D; ++l) {
+                    const C m = M.m[(j0 + jj) * D + l];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) cmad(acc[u], m, v[u][l][0]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) w[jj][u] = acc[u];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (u0 + (uint64_t)u * kThreads < n_units)
+                    st16(reinterpret_cast<float2 *>(sv) + base[u] + O.o[j0],
+                         make_float4(w[0][u].x, w[0][u].y, w[1][u].x, w[1][u].y));
+        }
+        return;
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const uint64_t unit = u0 + (uint64_t)u * kThreads;
