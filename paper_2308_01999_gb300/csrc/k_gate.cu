@@ -603,20 +603,21 @@ cudaError_t run_dense_blk(const LaunchCtx &L, void *sv, uint64_t n_sg, const Gro
 }
 
 // The warp-staged kernel takes a dense gate on a complex64 state when qubit 1
-// is a target (k = 2, 3) or all targets fall inside the block or three below
-// bit 5 (k = 4),
+// and a second target fall inside the block (k = 2, 3) or all targets fall
+// inside the block or three below bit 5 (k = 4),
 // every control sits at or above the block (bit B = 5 + the number of targets
 // below B) and at least one super-group exists. `G` holds
 // the sorted target and control positions; targets ascending in tpos.
 template <int K>
 bool try_dense_blk(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, const int *tpos, const MatK<float, K> &M,
                    cudaError_t &e) {
-    // k = 2, 3: qubit 1 a target; k = 4: all four targets inside the block, or
-    // three below bit 5. There the thread-per-group modes leave a warp's accesses
-    // spread thin (measured on the 28-qubit state: (0,1,2,3) 6.4 against 4.4
-    // TB/s); with fewer low targets a 4-qubit gate is faster in PAIR / T0 mode,
-    // whose two groups per thread share every matrix entry ((1,9,21,22) 6.1
-    // against 5.3, (0,1,9,20) 6.1 against 5.6, (3,4,9,14) 6.3 against 5.6)
+    // k = 2, 3: qubit 1 and a second target inside the block; k = 4: all four
+    // targets inside the block, or three below bit 5. There the thread-per-group
+    // modes leave a warp's accesses spread thin (measured on the 28-qubit state:
+    // (0,1,2,3) 6.4 against 4.4 TB/s); with fewer low targets PAIR / T0 mode is
+    // faster, its two groups per thread sharing every matrix entry ((1,9,21,22)
+    // 6.1 against 5.3, (0,1,9,20) 6.1 against 5.6, (3,4,9,14) 6.3 against 5.6,
+    // (1,9,12) 7.1 against 6.7, (1,9) 7.0 against 6.8)
     int klo = 0;
     while (klo < K && tpos[klo] < 5 + klo) ++klo;   // B = 5 + klo with klo targets below B
     bool t1 = false;
@@ -625,7 +626,7 @@ bool try_dense_blk(const LaunchCtx &L, void *sv, int n, const GroupGeom &G, cons
         t1 |= tpos[t] == 1;
         lo5 += tpos[t] < 5;
     }
-    if (K >= 4 ? !(klo == K || lo5 >= 3) : !t1) return false;
+    if (K >= 4 ? !(klo == K || lo5 >= 3) : !(t1 && klo >= 2)) return false;
     const int B = 5 + klo;
     GroupGeom Ghi{};
     Ghi.cset = G.cset;
