@@ -2,8 +2,10 @@
 // Sec. II-B: gate application is memory-bound for small k, so every kernel here
 // is a single streaming pass that reads and writes each touched amplitude once).
 //
-// Three kernel families, all in place:
+// Kernel families, all in place:
 //   k_dense      dense 2^k x 2^k product per group, k <= 4, group data in registers;
+//   k_dense_blk  the same for k = 2..4 with two or more low targets, the low bits
+//                staged through shared memory by warps;
 //   k_dense5     dense product for k = 5 in complex64, one group per thread in
 //                registers, the matrix broadcast from shared memory;
 //   k_dense6     the same for k = 6, a group over a pair of lanes;
@@ -211,9 +213,10 @@ k_dense(typename CT<R>::T *__restrict__ sv, uint64_t n_units, GroupGeom G, Offs<
 // ---------------------------------------------------------------------------
 // dense, k = 2..4, complex64, low targets: warp-staged super-groups
 // ---------------------------------------------------------------------------
-// With qubit 1 a target, consecutive groups (or group pairs) start 32 bytes or
-// more apart, so the thread-per-group access modes above touch only part of
-// every sector per instruction. Here the low bits are taken as a block: with
+// With two or more low targets (qubit 1 among them), consecutive groups (or
+// group pairs) start 32 bytes or more apart, so the thread-per-group access
+// modes above touch only part of every sector per instruction. Here the low
+// bits are taken as a block: with
 // KLO targets below bit B = 5 + KLO, the 2^B amplitudes of bits 0 .. B-1 hold
 // 32 whole groups' low members, contiguous in memory (2^B * 8 >= 512 bytes).
 // A warp takes one super-group -- fixed values of every bit at or above B that
