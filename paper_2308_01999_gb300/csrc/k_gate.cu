@@ -367,7 +367,10 @@ k_dense5(float2 *__restrict__ sv, uint64_t n_groups, GroupGeom G, Offs<5> O, con
         // so the 32 load addresses (64 registers) are not kept alive for them
         float2 *ps;
         asm volatile("mov.b64 %0, %1;" : "=l"(ps) : "l"(sv + base));
-#pragma unroll
+        // the batch loop stays rolled: unrolled, the kernel's 4096 FMAs per group
+        // overflow the instruction cache (instruction-fetch stalls led the warp
+        // states) and ran 20 % slower
+#pragma unroll 1
         for (int j0 = 0; j0 < 32; j0 += 8) {
             float2 acc[8];
 #pragma unroll
