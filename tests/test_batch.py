@@ -390,6 +390,16 @@ def test_cnot_times_one_qubit_blocks_are_split_on_host(svmod):
         assert b.compile([(n, gates, np.zeros((0, n)))], 2, 0)["ops"] == 1      # no windows: no split
         assert b.program_stats()["dense_ops"] == 1
         b.close()
+    # before a compile, and with no output array, the stats call is rejected
+    import ctypes as C
+    h = C.c_void_p()
+    assert sv.lib().sv_batch_create(None, C.byref(h)) == 0
+    try:
+        out = (C.c_uint64 * sv.SV_BATCH_STATS)()
+        assert sv.lib().sv_batch_program_stats(h, out) == 1            # SV_ERR_INVALID_ARGUMENT
+        assert sv.lib().sv_batch_program_stats(h, None) == 1
+    finally:
+        sv.lib().sv_batch_destroy(h)
 
 
 @pytest.mark.gpu

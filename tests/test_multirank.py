@@ -58,3 +58,9 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # the same `config` object as the GPU arm's line for this workload and world size
+    sys.path.insert(0, ROOT)
+    import bench
+    bench.N_QUBITS = 10
+    gates, paulis, _ = bench.workload()
+    assert d["config"] == json.loads(json.dumps(bench.line_config(2, len(gates), bench.step_bytes(gates, paulis))))
