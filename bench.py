@@ -400,10 +400,12 @@ def run_ours(args):
     del s, psi
     torch.cuda.empty_cache()
     if world == 1 and not args.main_only:
-        # the 30-qubit size of the bandwidth target, the 32-qubit fused circuit
-        # and the other two parts of the headline metric, on the same GPU after
-        # the 28-qubit step (rank 0 at N = 1 only, like the CPU baseline)
+        # the 30-qubit size of the bandwidth target, the bandwidth by number of
+        # targets (complex64, 20 random sets per width), the 32-qubit fused
+        # circuit and the other two parts of the headline metric, on the same
+        # GPU after the 28-qubit step (rank 0 at N = 1 only, like the CPU baseline)
         line["n30"] = n30_section(args)
+        line["e1"] = e1_section(20, 0)
         line["fused32"] = fused32_section(args)
         line["batch"] = batch_section(args)
         line["serve"] = serve_section(args)
@@ -598,11 +600,15 @@ def fused32_section(args, n: int = 32) -> dict:
 
 
 def run_e1(args):
+    print(json.dumps(e1_section(args.e1_sets, args.e1_sets_c128)))
+
+
+def e1_section(sets_c64: int, sets_c128: int) -> dict:
     """Gate-application bandwidth by number of targets (the paper's Sec. II-B
-    experiment): for k = 1..6, `--e1-sets` random target sets (sorted, seeded)
+    experiment): for k = 1..6, `sets_c64` random target sets (sorted, seeded)
     with a random dense 2^k x 2^k matrix each, one sv_apply_matrix launch per
-    set on a 33-qubit complex64 state (64 GiB) and `--e1-sets-c128` sets on a
-    32-qubit complex128 state (64 GiB), each launch timed with CUDA events on
+    set on a 33-qubit complex64 state (64 GiB) and `sets_c128` sets on a
+    32-qubit complex128 state (64 GiB; none: skipped), each launch timed with CUDA events on
     the handle's stream (the state is 500 times L2, so no launch finds its
     input in cache). Algorithmic bytes per launch: one read and one write of
     the state. Per k: median, 10th/90th percentile, min and max GB/s, and the
@@ -615,8 +621,11 @@ def run_e1(args):
     stream = torch.cuda.Stream(dev)
     peak, kind = load_peaks()
     out = {"workload": "random dense k-qubit gates, k = 1..6, one launch each", "peak_gbs": peak, "peak_kind": kind}
-    for name, n, dtype, sets in (("c64_33q", 33, torch.complex64, args.e1_sets),
-                                 ("c128_32q", 32, torch.complex128, args.e1_sets_c128)):
+    torch.cuda.empty_cache()
+    for name, n, dtype, sets in (("c64_33q", 33, torch.complex64, sets_c64),
+                                 ("c128_32q", 32, torch.complex128, sets_c128)):
+        if sets <= 0:
+            continue
         rng = gen.rng_for(2308 + n)
         nbytes = 2 * (1 << n) * (8 if dtype == torch.complex64 else 16)
         rec = {}
@@ -646,7 +655,7 @@ def run_e1(args):
         del psi
         torch.cuda.empty_cache()
         out[name] = rec
-    print(json.dumps(out))
+    return out
 
 
 def n30_section(args, n: int = 30) -> dict:
